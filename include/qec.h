@@ -1,0 +1,186 @@
+/*
+ * qec.h -- C ABI of the GB300 parallel sparse-blossom decoder.
+ *
+ * The decoder solves the minimum-weight embedded matching problem of the
+ * paper's "Decoding task" paragraph: given a detector graph G = (V, E) with
+ * positive integer edge weights, boundary edges, observable masks on edges and
+ * a set D of active detectors, find a minimum-weight edge set M whose degree is
+ * odd exactly at the detectors in D (boundary vertices: any degree), and return
+ * its weight and the XOR of the observable masks of its edges.  It runs sparse
+ * blossom (SI Sec. S1: graph-fill regions, events (a)-(g), flooder events
+ * ARRIVE / COLLIDE / IMPLODE) on the processing clusters of Algorithm 1 with
+ * the hierarchical execution rule of Algorithm 2 (Methods).
+ *
+ * Every pointer is a plain host or device pointer as stated per argument; no
+ * type of any framework appears here.  All calls are thread-compatible: a
+ * qec_graph may be used by several threads at once for decoding; create and
+ * destroy must not race with its use.
+ *
+ * Return codes: QEC_OK (0) or a negative QEC_E* value.  Per-shot outcomes are
+ * written to status arrays as QEC_SHOT_* values.
+ */
+#ifndef QEC_H_
+#define QEC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes -- */
+enum {
+    QEC_OK = 0,
+    QEC_EINVAL = -1,   /* bad argument: malformed graph, null pointer, size out of range */
+    QEC_ENOMEM = -2,   /* host or device allocation failed */
+    QEC_ECUDA = -3,    /* a CUDA runtime call failed (see qec_last_error) */
+    QEC_EAGAIN = -4,   /* serving: admission is full, retry after polling */
+    QEC_ERANGE = -5    /* a size exceeds a documented maximum */
+};
+
+enum {
+    QEC_SHOT_OK = 0,
+    QEC_SHOT_NO_SOLUTION = 1,     /* odd number of events in a part with no boundary */
+    QEC_SHOT_BUDGET_EXCEEDED = 2, /* event budget hit; the kernel stopped, no hang */
+    QEC_SHOT_CAPACITY = 3,        /* per-shot working set exceeds the largest slab */
+    QEC_SHOT_INTERNAL = 4         /* an internal consistency check failed */
+};
+
+#define QEC_MAX_GRAPHS_PER_BATCH 32
+#define QEC_MAX_OBSERVABLES 64
+
+typedef struct qec_graph qec_graph;
+typedef struct qec_stream qec_stream;
+/* cudaStream_t, passed as an opaque pointer (NULL = legacy default stream). */
+typedef void *qec_cuda_stream;
+
+/* Algorithm 3 inputs (Methods, "Finite-size parameter schedule"):
+ * q = q_num / q_den, phi_min = phi_num / phi_den, both in (0, 1).
+ * NULL in qec_graph_desc means q = 1/10, phi_min = 1/100 (the paper's choice,
+ * Methods "Numerical evaluation"). */
+typedef struct {
+    int32_t q_num, q_den;
+    int32_t phi_num, phi_den;
+} qec_params;
+
+/* Detector graph (paper "Decoding task").  num_edges physical edges; edge i
+ * joins detectors u[i] and v[i], or u[i] and its own boundary vertex when
+ * v[i] < 0.  w[i] > 0 is the integer weight (e.g. round(16 ln((1-p)/p)));
+ * obs[i] is the bit mask of logical observables the edge flips.  Parallel
+ * edges are merged: the merged edge keeps the smallest weight (ties: lowest
+ * input index) and that edge's mask; merged edges are ordered by
+ * (min endpoint, max endpoint) with a boundary partner sorting last, and the
+ * merged index decides ties between equally short boundary paths. */
+typedef struct {
+    int32_t num_detectors;     /* 1 .. 2^26 */
+    int32_t num_edges;         /* 0 .. 2^28 */
+    int32_t num_observables;   /* 0 .. 64 */
+    const int32_t *u;          /* host, [num_edges] */
+    const int32_t *v;          /* host, [num_edges], < 0 = boundary */
+    const int32_t *w;          /* host, [num_edges], 1 .. 2^20 */
+    const uint64_t *obs;       /* host, [num_edges] */
+    const qec_params *params;  /* host or NULL */
+} qec_graph_desc;
+
+/* Information about a created graph. */
+typedef struct {
+    int32_t num_detectors;
+    int32_t num_merged_edges;
+    int32_t words_per_shot;    /* uint32 words of one padded syndrome row (multiple of 4) */
+    int32_t wmax_internal;     /* largest merged weight x 2 */
+    int32_t num_levels;        /* levels of the Alg. 3 schedule stored below */
+    int64_t d_k[8];            /* Alg. 3 diameters d_k^V, internal units (level k at [k-1]) */
+    int64_t b_k[8];            /* Alg. 3 buffers b_k^V, internal units */
+    int32_t device;            /* CUDA device holding the graph */
+    int32_t has_internal_obs;  /* some detector-detector edge carries an observable */
+} qec_graph_info;
+
+/* Algorithm 3 (Methods, "Finite-size parameter schedule") for a graph whose
+ * largest internal weight (2 x the largest merged integer weight) is
+ * wmax_internal: d_1 = wmax_internal + 1, phi_1 = 1; b_k is the smallest
+ * integer with b_k >= d_k, phi_k > 2 d_k / b_k and Phi_{k+1}(b_k) >= phibar_{k+1};
+ * phi_{k+1} = Phi_{k+1}(b_k); d_{k+1} = 3 d_k + 4 b_k + 2 wmax_internal.  Exact
+ * rational arithmetic; stops early when a value would exceed 2^61.  Host only,
+ * no device needed.  Writes up to max_levels entries to d_k / b_k (host
+ * arrays, level k at index k-1) and returns the number of levels written
+ * (>= 1), or QEC_EINVAL for bad arguments. */
+int qec_schedule(int32_t wmax_internal, const qec_params *params, int64_t *d_k, int64_t *b_k,
+                 int32_t max_levels);
+
+/* Create a graph: validates and copies the host arrays, merges parallel edges,
+ * computes the Alg. 3 schedule with exact rational arithmetic, and uploads a
+ * CSR copy to the current CUDA device, which the library owns until
+ * qec_graph_destroy.  Errors: QEC_EINVAL (endpoint out of range, self loop,
+ * weight <= 0, more than 64 observables, bad params), QEC_ERANGE (size limits
+ * above), QEC_ENOMEM, QEC_ECUDA.  *out is NULL on failure. */
+int qec_graph_create(const qec_graph_desc *desc, qec_graph **out);
+int qec_graph_destroy(qec_graph *g);
+int qec_graph_get_info(const qec_graph *g, qec_graph_info *out);
+
+/* Copy the merged edge list to host arrays of qec_graph_info.num_merged_edges
+ * entries (u, v with -1 = boundary, internal weight = 2w, obs).  Any pointer may
+ * be NULL. */
+int qec_graph_merged_edges(const qec_graph *g, int32_t *u, int32_t *v, int32_t *w_internal,
+                           uint64_t *obs);
+
+/* Decode a batch of shots on the caller's stream (Alg. 1 + Alg. 2, SI S1).
+ *
+ * graphs            host array [num_graphs] (1 .. QEC_MAX_GRAPHS_PER_BATCH),
+ *                   all created on the current device.
+ * graph_of_shot     device [num_shots] int32 index into graphs, or NULL: every
+ *                   shot uses graphs[0].
+ * syn_offset_words  device [num_shots] int64 offset of each shot's syndrome row
+ *                   in `syndromes` (in uint32 words, a multiple of 4), or NULL:
+ *                   shot s starts at s * words_per_shot(graphs[0]).
+ * syndromes         device uint32 rows: bit i of a row (word i/32, bit i%32,
+ *                   LSB first) is detector i; words_per_shot words per row.
+ * obs_out           device [num_shots] uint64 predicted observable flips.
+ * weight_out        device [num_shots] int64 matching weight (original units).
+ * status_out        device [num_shots] int32 QEC_SHOT_* code.
+ * stream            cudaStream_t or NULL.
+ *
+ * The call enqueues work and returns without synchronising.  Scratch memory
+ * comes from a library-owned workspace on the device, grown on first use
+ * (that growth synchronises the device once); calls that share the workspace
+ * are serialised on their streams by the library.  Errors: QEC_EINVAL (null
+ * output pointers, num_graphs out of range, graphs on another device),
+ * QEC_ENOMEM, QEC_ECUDA. num_shots == 0 is a no-op. */
+int qec_decode_batch(const qec_graph *const *graphs, int32_t num_graphs,
+                     const int32_t *graph_of_shot, const int64_t *syn_offset_words,
+                     const uint32_t *syndromes, int64_t num_shots,
+                     uint64_t *obs_out, int64_t *weight_out, int32_t *status_out,
+                     qec_cuda_stream stream);
+
+/* Same as qec_decode_batch for one shot per kernel launch: shot s is decoded
+ * by its own launch of a one-warp grid (the plain per-shot GPU path). */
+int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_shots,
+                     uint64_t *obs_out, int64_t *weight_out, int32_t *status_out,
+                     qec_cuda_stream stream);
+
+/* Tuning knobs of the batched path (chosen by the autotuner in the Python
+ * binding; all have safe defaults).  Zero keeps the current value. */
+typedef struct {
+    int32_t warps_per_block;   /* 1 .. 32 */
+    int32_t blocks_per_sm;     /* 1 .. 64 */
+    int32_t band_factor;       /* flooder band width in units of the largest weight, 1 .. 64 */
+    int32_t kcap;              /* detection events per shot held by a main-pass slab */
+    int64_t max_events;        /* event budget per shot */
+} qec_tuning;
+int qec_set_tuning(const qec_tuning *t);
+int qec_get_tuning(qec_tuning *t);
+
+/* Release the library-owned device workspace of the current device. */
+int qec_release_workspace(void);
+
+/* Text of the most recent error of the calling thread (never NULL). */
+const char *qec_last_error(void);
+
+/* Version string. */
+const char *qec_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QEC_H_ */

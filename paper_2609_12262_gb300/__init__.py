@@ -1,0 +1,248 @@
+"""Python binding of the GB300 parallel sparse-blossom decoder (include/qec.h).
+
+Argument marshalling only: every step of decoding runs in the CUDA kernels of
+libqec.so.  PyTorch supplies device memory and streams.  Importing the package
+does not need a GPU; calling a decode without the built library raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libqec.so")
+
+QEC_OK, QEC_EINVAL, QEC_ENOMEM, QEC_ECUDA, QEC_EAGAIN, QEC_ERANGE = 0, -1, -2, -3, -4, -5
+SHOT_OK, SHOT_NO_SOLUTION, SHOT_BUDGET_EXCEEDED, SHOT_CAPACITY, SHOT_INTERNAL = 0, 1, 2, 3, 4
+MAX_GRAPHS_PER_BATCH = 32
+
+
+class QecError(RuntimeError):
+    pass
+
+
+class qec_params(C.Structure):
+    _fields_ = [("q_num", C.c_int32), ("q_den", C.c_int32), ("phi_num", C.c_int32), ("phi_den", C.c_int32)]
+
+
+class qec_graph_desc(C.Structure):
+    _fields_ = [
+        ("num_detectors", C.c_int32), ("num_edges", C.c_int32), ("num_observables", C.c_int32),
+        ("u", C.POINTER(C.c_int32)), ("v", C.POINTER(C.c_int32)), ("w", C.POINTER(C.c_int32)),
+        ("obs", C.POINTER(C.c_uint64)), ("params", C.POINTER(qec_params)),
+    ]
+
+
+class qec_graph_info(C.Structure):
+    _fields_ = [
+        ("num_detectors", C.c_int32), ("num_merged_edges", C.c_int32), ("words_per_shot", C.c_int32),
+        ("wmax_internal", C.c_int32), ("num_levels", C.c_int32),
+        ("d_k", C.c_int64 * 8), ("b_k", C.c_int64 * 8), ("device", C.c_int32),
+        ("has_internal_obs", C.c_int32),
+    ]
+
+
+class qec_tuning(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("band_factor", C.c_int32),
+                ("kcap", C.c_int32), ("max_events", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libqec.so (raises QecError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise QecError("libqec.so is not built (run paper_2609_12262_gb300.build.build())")
+    L = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    vp = C.c_void_p
+    L.qec_last_error.restype = C.c_char_p
+    L.qec_version.restype = C.c_char_p
+    L.qec_schedule.argtypes = [C.c_int32, P(qec_params), P(C.c_int64), P(C.c_int64), C.c_int32]
+    L.qec_graph_create.argtypes = [P(qec_graph_desc), P(vp)]
+    L.qec_graph_destroy.argtypes = [vp]
+    L.qec_graph_get_info.argtypes = [vp, P(qec_graph_info)]
+    L.qec_graph_merged_edges.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_uint64)]
+    L.qec_decode_batch.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+    L.qec_decode_plain.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
+    L.qec_set_tuning.argtypes = [P(qec_tuning)]
+    L.qec_get_tuning.argtypes = [P(qec_tuning)]
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return lib().qec_last_error().decode()
+
+
+def version() -> str:
+    return lib().qec_version().decode()
+
+
+def _check(rc):
+    if rc != QEC_OK:
+        raise QecError("qec error %d: %s" % (rc, last_error()))
+    return rc
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def schedule(wmax_internal: int, q=(1, 10), phi_min=(1, 100), levels: int = 8):
+    """Algorithm 3 via qec_schedule: returns (d_k list, b_k list), internal units."""
+    L = lib()
+    d = np.zeros(levels, np.int64)
+    b = np.zeros(levels, np.int64)
+    p = qec_params(q[0], q[1], phi_min[0], phi_min[1])
+    n = L.qec_schedule(int(wmax_internal), C.byref(p), _ptr(d, C.c_int64), _ptr(b, C.c_int64), levels)
+    if n < 1:
+        raise QecError(last_error())
+    return d[:n].tolist(), b[:n].tolist()
+
+
+class Graph:
+    """A detector graph resident on the current CUDA device (qec_graph_create)."""
+
+    def __init__(self, num_detectors, u, v, w, obs, num_observables: int = 1, q=None, phi_min=None):
+        L = lib()
+        self._u = np.ascontiguousarray(u, np.int32)
+        self._v = np.ascontiguousarray(v, np.int32)
+        self._w = np.ascontiguousarray(w, np.int32)
+        self._o = np.ascontiguousarray(obs, np.uint64)
+        desc = qec_graph_desc()
+        desc.num_detectors = int(num_detectors)
+        desc.num_edges = int(self._u.shape[0])
+        desc.num_observables = int(num_observables)
+        desc.u = _ptr(self._u, C.c_int32)
+        desc.v = _ptr(self._v, C.c_int32)
+        desc.w = _ptr(self._w, C.c_int32)
+        desc.obs = _ptr(self._o, C.c_uint64)
+        self._params = None
+        if q is not None or phi_min is not None:
+            q = q or (1, 10)
+            phi_min = phi_min or (1, 100)
+            self._params = qec_params(q[0], q[1], phi_min[0], phi_min[1])
+            desc.params = C.pointer(self._params)
+        h = C.c_void_p()
+        _check(L.qec_graph_create(C.byref(desc), C.byref(h)))
+        self._h = h
+        info = qec_graph_info()
+        _check(L.qec_graph_get_info(h, C.byref(info)))
+        self.info = info
+        self.num_detectors = info.num_detectors
+        self.words = info.words_per_shot
+
+    @classmethod
+    def from_phys(cls, g, **kw):
+        return cls(g.num_detectors, g.u, g.v, g.w, g.obs, **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def schedule(self):
+        n = self.info.num_levels
+        return list(self.info.d_k)[:n], list(self.info.b_k)[:n]
+
+    def merged_edges(self):
+        m = self.info.num_merged_edges
+        u = np.zeros(m, np.int32); v = np.zeros(m, np.int32)
+        w = np.zeros(m, np.int32); o = np.zeros(m, np.uint64)
+        _check(lib().qec_graph_merged_edges(self._h, _ptr(u, C.c_int32), _ptr(v, C.c_int32),
+                                            _ptr(w, C.c_int32), _ptr(o, C.c_uint64)))
+        return u, v, w, o
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().qec_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def decode_batch(graphs, syndromes, graph_of_shot=None, syn_offset_words=None, num_shots=None,
+                 out=None, stream=None):
+    """qec_decode_batch on torch device tensors.
+
+    syndromes: int32 CUDA tensor holding the uint32 syndrome rows (flat or 2-D).
+    graph_of_shot: int32 CUDA tensor or None; syn_offset_words: int64 CUDA tensor or None.
+    Returns (obs int64 [S] holding the uint64 bits, weight int64 [S], status int32 [S]).
+    """
+    import torch
+    if isinstance(graphs, Graph):
+        graphs = [graphs]
+    if num_shots is None:
+        if graph_of_shot is not None:
+            num_shots = int(graph_of_shot.shape[0])
+        else:
+            num_shots = int(syndromes.numel() // graphs[0].words)
+    dev = syndromes.device
+    if out is None:
+        out = (torch.empty(num_shots, dtype=torch.int64, device=dev),
+               torch.empty(num_shots, dtype=torch.int64, device=dev),
+               torch.empty(num_shots, dtype=torch.int32, device=dev))
+    obs, w, st = out
+    arr = (C.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    _check(lib().qec_decode_batch(arr, len(graphs), _dptr(graph_of_shot), _dptr(syn_offset_words),
+                                  _dptr(syndromes), int(num_shots), _dptr(obs), _dptr(w), _dptr(st),
+                                  _stream_handle(stream)))
+    return obs, w, st
+
+
+def decode_plain(graph, syndromes, num_shots=None, out=None, stream=None):
+    """qec_decode_plain: one kernel launch per shot (the plain GPU path)."""
+    import torch
+    if num_shots is None:
+        num_shots = int(syndromes.numel() // graph.words)
+    dev = syndromes.device
+    if out is None:
+        out = (torch.empty(num_shots, dtype=torch.int64, device=dev),
+               torch.empty(num_shots, dtype=torch.int64, device=dev),
+               torch.empty(num_shots, dtype=torch.int32, device=dev))
+    obs, w, st = out
+    _check(lib().qec_decode_plain(graph.handle, _dptr(syndromes), int(num_shots), _dptr(obs), _dptr(w),
+                                  _dptr(st), _stream_handle(stream)))
+    return obs, w, st
+
+
+def set_tuning(warps_per_block=0, blocks_per_sm=0, band_factor=0, kcap=0, max_events=0):
+    t = qec_tuning(int(warps_per_block), int(blocks_per_sm), int(band_factor), int(kcap), int(max_events))
+    _check(lib().qec_set_tuning(C.byref(t)))
+
+
+def get_tuning() -> dict:
+    t = qec_tuning()
+    _check(lib().qec_get_tuning(C.byref(t)))
+    return {f: getattr(t, f) for f, _ in qec_tuning._fields_}
+
+
+def release_workspace():
+    _check(lib().qec_release_workspace())
+
+
+def to_uint64(t) -> np.ndarray:
+    """int64 tensor holding uint64 bits -> numpy uint64."""
+    return t.detach().cpu().numpy().view(np.uint64)

@@ -1,0 +1,592 @@
+// capi.cpp -- host side of the C ABI declared in include/qec.h.
+//
+// Graph creation (validation, parallel-edge merging, CSR upload, Algorithm 3
+// schedule in exact rational arithmetic), the device workspace and the batch /
+// plain launch paths.  Kernels live in decoder.cu.
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qec_internal.h"
+
+using qec::BatchArgs;
+using qec::DGraph;
+using qec::SlabCaps;
+using qec::Slot;
+
+struct qec_graph {
+    int device = -1;
+    int n = 0;
+    int m = 0;                      // merged edges
+    int words = 0;
+    int wmax = 0;                   // internal
+    int internal_obs = 0;
+    int num_levels = 0;
+    long long dk[8] = {0}, bk[8] = {0};
+    std::vector<int> eu, ev, ew;    // merged edges (host copy)
+    std::vector<unsigned long long> eobs;
+    int *d_row = nullptr;
+    Slot *d_slot = nullptr;
+    unsigned long long *d_eobs = nullptr;
+    int2 *d_eend = nullptr;
+    DGraph dg{};
+};
+
+namespace {
+
+thread_local std::string g_err = "";
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return QEC_ECUDA;
+}
+
+// ------------------------------------------------------------ rationals --
+// Exact rationals on __int128 with overflow detection, for Algorithm 3.
+struct Q {
+    __int128 n, d;   // d > 0, gcd(n, d) == 1
+};
+
+__int128 gcd128(__int128 a, __int128 b) {
+    if (a < 0) a = -a;
+    if (b < 0) b = -b;
+    while (b) { __int128 t = a % b; a = b; b = t; }
+    return a ? a : 1;
+}
+
+bool mk(__int128 n, __int128 d, Q &out) {
+    if (d == 0) return false;
+    if (d < 0) { n = -n; d = -d; }
+    __int128 g = gcd128(n, d);
+    out.n = n / g;
+    out.d = d / g;
+    return true;
+}
+
+bool mul128(__int128 a, __int128 b, __int128 &r) { return !__builtin_mul_overflow(a, b, &r); }
+bool add128(__int128 a, __int128 b, __int128 &r) { return !__builtin_add_overflow(a, b, &r); }
+
+bool qadd(Q a, Q b, Q &r) {
+    __int128 x, y, z, w;
+    if (!mul128(a.n, b.d, x) || !mul128(b.n, a.d, y) || !add128(x, y, z) || !mul128(a.d, b.d, w)) return false;
+    return mk(z, w, r);
+}
+bool qneg(Q a, Q &r) { r.n = -a.n; r.d = a.d; return true; }
+bool qsub(Q a, Q b, Q &r) { Q nb; qneg(b, nb); return qadd(a, nb, r); }
+bool qmul(Q a, Q b, Q &r) {
+    __int128 x, w;
+    if (!mul128(a.n, b.n, x) || !mul128(a.d, b.d, w)) return false;
+    return mk(x, w, r);
+}
+bool qdiv(Q a, Q b, Q &r) {
+    if (b.n == 0) return false;
+    __int128 x, w;
+    if (!mul128(a.n, b.d, x) || !mul128(a.d, b.n, w)) return false;
+    return mk(x, w, r);
+}
+// sign of a - b, or 2 on overflow
+int qcmp(Q a, Q b) {
+    __int128 x, y;
+    if (!mul128(a.n, b.d, x) || !mul128(b.n, a.d, y)) return 2;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+Q qint(long long v) { return Q{(__int128)v, 1}; }
+__int128 qfloor(Q a) {
+    __int128 f = a.n / a.d;
+    if ((a.n % a.d != 0) && (a.n < 0)) f -= 1;
+    return f;
+}
+__int128 qceil(Q a) { return -qfloor(Q{-a.n, a.d}); }
+
+// Phi_{k+1}(b) = phi - (phi + 2) d / ((phi + 1) d + phi b)
+bool big_phi(Q phi, long long d, long long b, Q &out) {
+    Q two = qint(2), one = qint(1), dd = qint(d), bb = qint(b);
+    Q num, den, t1, t2, frac;
+    if (!qadd(phi, two, t1) || !qmul(t1, dd, num)) return false;
+    if (!qadd(phi, one, t1) || !qmul(t1, dd, t1) || !qmul(phi, bb, t2) || !qadd(t1, t2, den)) return false;
+    if (!qdiv(num, den, frac)) return false;
+    return qsub(phi, frac, out);
+}
+
+// admissible(b): b >= d, b > 0, phi > 2d/b, Phi(b) >= target.  -1 on overflow.
+int admissible(Q phi, long long d, long long b, Q target) {
+    if (b < d || b <= 0) return 0;
+    Q r;
+    if (!qdiv(qint(2 * d), qint(b), r)) return -1;
+    int c = qcmp(phi, r);
+    if (c == 2) return -1;
+    if (c <= 0) return 0;
+    Q p;
+    if (!big_phi(phi, d, b, p)) return -1;
+    c = qcmp(p, target);
+    if (c == 2) return -1;
+    return c >= 0 ? 1 : 0;
+}
+
+// Algorithm 3 (Methods, "Finite-size parameter schedule"), internal units.
+int schedule(int wmax, Q q, Q phimin, long long *dk, long long *bk, int maxlev) {
+    Q phi = qint(1);
+    long long d = (long long)wmax + 1;
+    int lev = 0;
+    for (int k = 1; k <= maxlev; k++) {
+        // phibar_{k+1} = phimin + (1 - phimin) q^k
+        Q qk = qint(1), t, one_m, target;
+        bool ok = true;
+        for (int i = 0; i < k && ok; i++) ok = qmul(qk, q, qk);
+        ok = ok && qsub(qint(1), phimin, one_m) && qmul(one_m, qk, t) && qadd(phimin, t, target);
+        if (!ok) break;
+        if (qcmp(phi, target) != 1) break;
+        // b > 2d / phi
+        Q r;
+        if (!qdiv(qint(2 * d), phi, r)) break;
+        __int128 lo1 = qfloor(r) + 1;
+        // Phi(b) >= target  <=>  b >= ((phi + 2) d / (phi - target) - (phi + 1) d) / phi
+        Q a1, a2, a3, a4, x;
+        if (!qadd(phi, qint(2), a1) || !qmul(a1, qint(d), a1) || !qsub(phi, target, a2) ||
+            !qdiv(a1, a2, a3) || !qadd(phi, qint(1), a4) || !qmul(a4, qint(d), a4) ||
+            !qsub(a3, a4, x) || !qdiv(x, phi, x))
+            break;
+        __int128 lo2 = qceil(x);
+        __int128 b = d;
+        if (lo1 > b) b = lo1;
+        if (lo2 > b) b = lo2;
+        if (b < 1) b = 1;
+        if (b > (__int128)(1LL << 61)) break;
+        long long bl = (long long)b;
+        if (admissible(phi, d, bl, target) != 1) break;
+        if (bl - 1 >= 1 && admissible(phi, d, bl - 1, target) != 0) break;
+        dk[lev] = d;
+        bk[lev] = bl;
+        lev++;
+        Q nphi;
+        if (!big_phi(phi, d, bl, nphi)) break;
+        phi = nphi;
+        __int128 nd = (__int128)3 * d + (__int128)4 * bl + (__int128)2 * wmax;
+        if (nd > (__int128)(1LL << 61)) break;
+        d = (long long)nd;
+    }
+    return lev;
+}
+
+struct PhysKey {
+    int lo, hi, w, idx;
+};
+
+// ------------------------------------------------------------ workspace --
+struct Workspace {
+    int device = -1;
+    char *slabs = nullptr;
+    long long slab_bytes = 0;
+    long long nwarps = 0;
+    SlabCaps caps{};
+    char *slabs2 = nullptr;          // overflow pass
+    long long slab_bytes2 = 0;
+    long long nwarps2 = 0;
+    SlabCaps caps2{};
+    unsigned long long *queue = nullptr;
+    int *overflow = nullptr;
+    long long overflow_cap = 0;
+    cudaEvent_t done = nullptr;
+    std::mutex mu;
+};
+
+Workspace g_ws[64];
+std::mutex g_tune_mu;
+qec_tuning g_tune = {4, 0, 1, 0, 4000000};
+
+void ws_free(Workspace &w) {
+    if (w.slabs) cudaFree(w.slabs);
+    if (w.slabs2) cudaFree(w.slabs2);
+    if (w.queue) cudaFree(w.queue);
+    if (w.overflow) cudaFree(w.overflow);
+    if (w.done) cudaEventDestroy(w.done);
+    w.slabs = w.slabs2 = nullptr;
+    w.queue = nullptr;
+    w.overflow = nullptr;
+    w.done = nullptr;
+    w.slab_bytes = w.slab_bytes2 = 0;
+    w.nwarps = w.nwarps2 = 0;
+    w.overflow_cap = 0;
+}
+
+int kcap_for(int nmax, const qec_tuning &t) {
+    if (t.kcap > 0) return std::min(t.kcap, std::max(1, nmax));
+    int k = nmax / 16;
+    k = std::max(64, std::min(1024, k));
+    return std::min(k, std::max(nmax, 1));
+}
+
+// Make sure the workspace of `dev` fits the request; may synchronise the device.
+int ws_ensure(Workspace &w, int dev, const SlabCaps &caps, long long nwarps, const SlabCaps &caps2,
+              long long nwarps2, long long nshots) {
+    w.device = dev;
+    const long long sb = qec::slab_bytes_for(caps);
+    const long long sb2 = qec::slab_bytes_for(caps2);
+    cudaError_t e;
+    if (!w.done) {
+        e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+        e = cudaEventRecord(w.done, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    }
+    const bool grow1 = sb * nwarps > w.slab_bytes * w.nwarps || sb != w.slab_bytes || nwarps > w.nwarps;
+    const bool grow2 = sb2 * nwarps2 > w.slab_bytes2 * w.nwarps2 || sb2 != w.slab_bytes2 || nwarps2 > w.nwarps2;
+    const bool grow3 = nshots > w.overflow_cap || !w.queue;
+    if (grow1 || grow2 || grow3) {
+        e = cudaEventSynchronize(w.done);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    }
+    if (grow1) {
+        if (w.slabs) cudaFree(w.slabs);
+        w.slabs = nullptr;
+        e = cudaMalloc(&w.slabs, (size_t)(sb * nwarps));
+        if (e != cudaSuccess) { w.slab_bytes = 0; w.nwarps = 0; return fail(QEC_ENOMEM, "workspace allocation failed"); }
+        w.slab_bytes = sb;
+        w.nwarps = nwarps;
+    }
+    w.caps = caps;
+    if (grow2) {
+        if (w.slabs2) cudaFree(w.slabs2);
+        w.slabs2 = nullptr;
+        e = cudaMalloc(&w.slabs2, (size_t)(sb2 * nwarps2));
+        if (e != cudaSuccess) { w.slab_bytes2 = 0; w.nwarps2 = 0; return fail(QEC_ENOMEM, "workspace allocation failed"); }
+        w.slab_bytes2 = sb2;
+        w.nwarps2 = nwarps2;
+    }
+    w.caps2 = caps2;
+    if (grow3) {
+        if (!w.queue) {
+            e = cudaMalloc(&w.queue, 4 * sizeof(unsigned long long));
+            if (e != cudaSuccess) return fail(QEC_ENOMEM, "workspace allocation failed");
+        }
+        if (w.overflow) cudaFree(w.overflow);
+        w.overflow = nullptr;
+        long long cap = std::max<long long>(nshots, 1024);
+        e = cudaMalloc(&w.overflow, (size_t)cap * sizeof(int));
+        if (e != cudaSuccess) { w.overflow_cap = 0; return fail(QEC_ENOMEM, "workspace allocation failed"); }
+        w.overflow_cap = cap;
+    }
+    return QEC_OK;
+}
+
+int sm_count(int dev) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qec_last_error(void) { return g_err.c_str(); }
+
+const char *qec_version(void) { return "qec-sparse-blossom-gb300 0.1 (sm_103a)"; }
+
+int qec_schedule(int32_t wmax_internal, const qec_params *params, int64_t *d_k, int64_t *b_k,
+                 int32_t max_levels) {
+    if (wmax_internal < 1 || !d_k || !b_k || max_levels < 1 || max_levels > 64)
+        return fail(QEC_EINVAL, "bad schedule arguments");
+    Q q = {1, 10}, phimin = {1, 100};
+    if (params) {
+        if (params->q_den <= 0 || params->phi_den <= 0 || params->q_num <= 0 || params->phi_num <= 0 ||
+            params->q_num >= params->q_den || params->phi_num >= params->phi_den)
+            return fail(QEC_EINVAL, "params must be fractions in (0, 1)");
+        mk(params->q_num, params->q_den, q);
+        mk(params->phi_num, params->phi_den, phimin);
+    }
+    std::vector<long long> dk((size_t)max_levels), bk((size_t)max_levels);
+    const int lev = schedule(wmax_internal, q, phimin, dk.data(), bk.data(), max_levels);
+    for (int i = 0; i < lev; i++) { d_k[i] = dk[i]; b_k[i] = bk[i]; }
+    return lev >= 1 ? lev : fail(QEC_EINVAL, "no admissible level-1 parameters");
+}
+
+int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
+    if (!out) return fail(QEC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(QEC_EINVAL, "desc is NULL");
+    const int n = desc->num_detectors, m = desc->num_edges;
+    if (n < 1 || n > (1 << 26)) return fail(QEC_ERANGE, "num_detectors out of range");
+    if (m < 0 || m > (1 << 28)) return fail(QEC_ERANGE, "num_edges out of range");
+    if (desc->num_observables < 0 || desc->num_observables > QEC_MAX_OBSERVABLES)
+        return fail(QEC_EINVAL, "num_observables out of range");
+    if (m > 0 && (!desc->u || !desc->v || !desc->w || !desc->obs)) return fail(QEC_EINVAL, "edge array is NULL");
+    Q q = {1, 10}, phimin = {1, 100};
+    if (desc->params) {
+        const qec_params *p = desc->params;
+        if (p->q_den <= 0 || p->phi_den <= 0 || p->q_num <= 0 || p->phi_num <= 0 || p->q_num >= p->q_den ||
+            p->phi_num >= p->phi_den)
+            return fail(QEC_EINVAL, "params must be fractions in (0, 1)");
+        mk(p->q_num, p->q_den, q);
+        mk(p->phi_num, p->phi_den, phimin);
+    }
+    const unsigned long long obs_mask =
+        desc->num_observables >= 64 ? ~0ull : ((1ull << desc->num_observables) - 1ull);
+    std::vector<PhysKey> keys((size_t)m);
+    for (int i = 0; i < m; i++) {
+        const int a = desc->u[i], b = desc->v[i], w = desc->w[i];
+        if (a < 0 || a >= n || b >= n || a == b) return fail(QEC_EINVAL, "edge endpoint out of range or self loop");
+        if (w <= 0 || w > (1 << 20)) return fail(QEC_EINVAL, "edge weight must be in 1 .. 2^20");
+        if (desc->obs[i] & ~obs_mask) return fail(QEC_EINVAL, "observable bit beyond num_observables");
+        if (b < 0) keys[i] = PhysKey{a, INT32_MAX, w, i};
+        else keys[i] = PhysKey{std::min(a, b), std::max(a, b), w, i};
+    }
+    std::sort(keys.begin(), keys.end(), [](const PhysKey &x, const PhysKey &y) {
+        if (x.lo != y.lo) return x.lo < y.lo;
+        if (x.hi != y.hi) return x.hi < y.hi;
+        if (x.w != y.w) return x.w < y.w;
+        return x.idx < y.idx;
+    });
+    qec_graph *g = new (std::nothrow) qec_graph();
+    if (!g) return fail(QEC_ENOMEM, "host allocation failed");
+    for (int i = 0; i < m; i++) {
+        if (i > 0 && keys[i].lo == keys[i - 1].lo && keys[i].hi == keys[i - 1].hi) continue;
+        g->eu.push_back(keys[i].lo);
+        g->ev.push_back(keys[i].hi == INT32_MAX ? -1 : keys[i].hi);
+        g->ew.push_back(2 * keys[i].w);
+        g->eobs.push_back(desc->obs[keys[i].idx]);
+    }
+    g->n = n;
+    g->m = (int)g->eu.size();
+    g->words = ((n + 31) / 32 + 3) / 4 * 4;
+    for (int e = 0; e < g->m; e++) {
+        g->wmax = std::max(g->wmax, g->ew[e]);
+        if (g->ev[e] >= 0 && g->eobs[e] != 0) g->internal_obs = 1;
+    }
+    if ((long long)g->wmax * (long long)n > (1LL << 30)) {
+        delete g;
+        return fail(QEC_ERANGE, "largest weight x detectors exceeds 2^30 (distances are int32)");
+    }
+    g->num_levels = schedule(g->wmax, q, phimin, g->dk, g->bk, 8);
+    if (g->num_levels < 1) {
+        delete g;
+        return fail(QEC_EINVAL, "Algorithm 3 schedule has no admissible level-1 parameters");
+    }
+    // CSR: slots of each detector in merged-edge order
+    std::vector<int> row((size_t)n + 1, 0);
+    for (int e = 0; e < g->m; e++) {
+        row[g->eu[e] + 1]++;
+        if (g->ev[e] >= 0) row[g->ev[e] + 1]++;
+    }
+    for (int x = 0; x < n; x++) row[x + 1] += row[x];
+    std::vector<Slot> slots((size_t)row[n] + 1);
+    std::vector<int> fill((size_t)n, 0);
+    std::vector<int2> eend((size_t)g->m + 1);
+    for (int e = 0; e < g->m; e++) {
+        const int a = g->eu[e], b = g->ev[e];
+        slots[row[a] + fill[a]++] = Slot{b, g->ew[e], e, 0};
+        if (b >= 0) slots[row[b] + fill[b]++] = Slot{a, g->ew[e], e, 0};
+        eend[e] = make_int2(a, g->ew[e]);
+    }
+    cudaError_t ce = cudaGetDevice(&g->device);
+    if (ce != cudaSuccess) { delete g; return cuda_fail(ce, "cudaGetDevice"); }
+    const size_t nslots = (size_t)row[n] + 1, ne = (size_t)g->m + 1;
+    ce = cudaMalloc(&g->d_row, sizeof(int) * ((size_t)n + 1));
+    if (ce == cudaSuccess) ce = cudaMalloc(&g->d_slot, sizeof(Slot) * nslots);
+    if (ce == cudaSuccess) ce = cudaMalloc(&g->d_eobs, sizeof(unsigned long long) * ne);
+    if (ce == cudaSuccess) ce = cudaMalloc(&g->d_eend, sizeof(int2) * ne);
+    if (ce != cudaSuccess) { qec_graph_destroy(g); return fail(QEC_ENOMEM, "device allocation failed"); }
+    std::vector<unsigned long long> eo(g->eobs);
+    eo.push_back(0);
+    ce = cudaMemcpy(g->d_row, row.data(), sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(g->d_slot, slots.data(), sizeof(Slot) * nslots, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(g->d_eobs, eo.data(), sizeof(unsigned long long) * ne, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(g->d_eend, eend.data(), sizeof(int2) * ne, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) { qec_graph_destroy(g); return cuda_fail(ce, "cudaMemcpy"); }
+    DGraph &d = g->dg;
+    d.n = n;
+    d.words = g->words;
+    d.wmax = g->wmax;
+    d.d1 = (int)std::min<long long>(g->dk[0], INT32_MAX / 4);
+    d.b1 = (int)std::min<long long>(g->bk[0], INT32_MAX / 4);
+    d.internal_obs = g->internal_obs;
+    d.row = g->d_row;
+    d.slot = g->d_slot;
+    d.eobs = g->d_eobs;
+    d.eend = g->d_eend;
+    *out = g;
+    return QEC_OK;
+}
+
+int qec_graph_destroy(qec_graph *g) {
+    if (!g) return QEC_OK;
+    if (g->d_row) cudaFree(g->d_row);
+    if (g->d_slot) cudaFree(g->d_slot);
+    if (g->d_eobs) cudaFree(g->d_eobs);
+    if (g->d_eend) cudaFree(g->d_eend);
+    delete g;
+    return QEC_OK;
+}
+
+int qec_graph_get_info(const qec_graph *g, qec_graph_info *out) {
+    if (!g || !out) return fail(QEC_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->num_detectors = g->n;
+    out->num_merged_edges = g->m;
+    out->words_per_shot = g->words;
+    out->wmax_internal = g->wmax;
+    out->num_levels = g->num_levels;
+    for (int i = 0; i < g->num_levels && i < 8; i++) { out->d_k[i] = g->dk[i]; out->b_k[i] = g->bk[i]; }
+    out->device = g->device;
+    out->has_internal_obs = g->internal_obs;
+    return QEC_OK;
+}
+
+int qec_graph_merged_edges(const qec_graph *g, int32_t *u, int32_t *v, int32_t *w, uint64_t *obs) {
+    if (!g) return fail(QEC_EINVAL, "graph is NULL");
+    for (int e = 0; e < g->m; e++) {
+        if (u) u[e] = g->eu[e];
+        if (v) v[e] = g->ev[e];
+        if (w) w[e] = g->ew[e];
+        if (obs) obs[e] = g->eobs[e];
+    }
+    return QEC_OK;
+}
+
+int qec_set_tuning(const qec_tuning *t) {
+    if (!t) return fail(QEC_EINVAL, "NULL tuning");
+    if (t->warps_per_block < 0 || t->warps_per_block > 32 || t->blocks_per_sm < 0 || t->blocks_per_sm > 64 ||
+        t->band_factor < 0 || t->band_factor > 64 || t->kcap < 0 || t->max_events < 0)
+        return fail(QEC_EINVAL, "tuning value out of range");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (t->warps_per_block) g_tune.warps_per_block = t->warps_per_block;
+    if (t->blocks_per_sm) g_tune.blocks_per_sm = t->blocks_per_sm;
+    if (t->band_factor) g_tune.band_factor = t->band_factor;
+    if (t->kcap) g_tune.kcap = t->kcap;
+    if (t->max_events) g_tune.max_events = t->max_events;
+    return QEC_OK;
+}
+
+int qec_get_tuning(qec_tuning *t) {
+    if (!t) return fail(QEC_EINVAL, "NULL tuning");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *t = g_tune;
+    return QEC_OK;
+}
+
+int qec_release_workspace(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(QEC_EINVAL, "device index");
+    Workspace &w = g_ws[dev];
+    std::lock_guard<std::mutex> lk(w.mu);
+    if (w.done) cudaEventSynchronize(w.done);
+    ws_free(w);
+    return QEC_OK;
+}
+
+static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, const int32_t *graph_of_shot,
+                         const int64_t *syn_offset_words, const uint32_t *syndromes, int64_t num_shots,
+                         uint64_t *obs_out, int64_t *weight_out, int32_t *status_out, qec_cuda_stream stream,
+                         bool plain) {
+    if (num_shots < 0) return fail(QEC_EINVAL, "num_shots < 0");
+    if (num_shots == 0) return QEC_OK;
+    if (!graphs || num_graphs < 1 || num_graphs > QEC_MAX_GRAPHS_PER_BATCH)
+        return fail(QEC_EINVAL, "num_graphs out of range");
+    if (!syndromes || !obs_out || !weight_out || !status_out) return fail(QEC_EINVAL, "NULL buffer");
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(QEC_EINVAL, "device index");
+    int nmax = 1;
+    for (int i = 0; i < num_graphs; i++) {
+        if (!graphs[i]) return fail(QEC_EINVAL, "NULL graph");
+        if (graphs[i]->device != dev) return fail(QEC_EINVAL, "graph lives on another device");
+        nmax = std::max(nmax, graphs[i]->n);
+    }
+    qec_tuning tune;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune = g_tune;
+    }
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int sms = sm_count(dev);
+    const int kcap = kcap_for(nmax, tune);
+    SlabCaps caps = qec::caps_for_kcap(kcap);
+    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, std::min(nmax, 16 * kcap)));
+    const int wpb = std::max(1, tune.warps_per_block);
+    int bps = tune.blocks_per_sm;
+    if (bps <= 0) bps = std::max(1, 16 / wpb);
+    long long nwarps = plain ? 1 : (long long)sms * bps * wpb;
+    long long nwarps2 = plain ? 1 : (long long)sms;
+    if (plain) caps = caps2;
+    Workspace &w = g_ws[dev];
+    std::lock_guard<std::mutex> lk(w.mu);
+    int rc = ws_ensure(w, dev, caps, nwarps, caps2, nwarps2, plain ? 1 : num_shots);
+    if (rc != QEC_OK) return rc;
+    ce = cudaStreamWaitEvent(s, w.done, 0);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamWaitEvent");
+    BatchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int i = 0; i < num_graphs; i++) a.g[i] = graphs[i]->dg;
+    a.num_graphs = num_graphs;
+    a.band_factor = std::max(1, tune.band_factor);
+    a.num_shots = num_shots;
+    a.max_events = tune.max_events > 0 ? tune.max_events : 4000000;
+    a.graph_of_shot = graph_of_shot;
+    a.syn_off = reinterpret_cast<const long long *>(syn_offset_words);
+    a.syn = syndromes;
+    a.obs_out = reinterpret_cast<unsigned long long *>(obs_out);
+    a.w_out = reinterpret_cast<long long *>(weight_out);
+    a.st_out = status_out;
+    a.queue = w.queue;
+    a.overflow = w.overflow;
+    a.watchdog_ns = 60LL * 1000 * 1000 * 1000;
+    if (plain) {
+        a.slabs = w.slabs;
+        a.slab_bytes = w.slab_bytes;
+        a.caps = w.caps;
+        a.pass = 0;
+        for (int64_t shot = 0; shot < num_shots; shot++) {
+            a.single_shot = shot;
+            ce = qec::launch_batch(a, 1, 32, s);
+            if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
+        }
+    } else {
+        a.single_shot = -1;
+        ce = qec::launch_reset_queue(w.queue, s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemsetAsync");
+        a.slabs = w.slabs;
+        a.slab_bytes = w.slab_bytes;
+        a.caps = w.caps;
+        a.pass = 0;
+        ce = qec::launch_batch(a, (int)(nwarps / wpb), 32 * wpb, s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
+        a.slabs = w.slabs2;
+        a.slab_bytes = w.slab_bytes2;
+        a.caps = w.caps2;
+        a.pass = 1;
+        ce = qec::launch_batch(a, (int)nwarps2, 32, s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
+    }
+    ce = cudaEventRecord(w.done, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventRecord");
+    return QEC_OK;
+}
+
+int qec_decode_batch(const qec_graph *const *graphs, int32_t num_graphs, const int32_t *graph_of_shot,
+                     const int64_t *syn_offset_words, const uint32_t *syndromes, int64_t num_shots,
+                     uint64_t *obs_out, int64_t *weight_out, int32_t *status_out, qec_cuda_stream stream) {
+    return decode_common(graphs, num_graphs, graph_of_shot, syn_offset_words, syndromes, num_shots, obs_out,
+                         weight_out, status_out, stream, false);
+}
+
+int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_shots, uint64_t *obs_out,
+                     int64_t *weight_out, int32_t *status_out, qec_cuda_stream stream) {
+    const qec_graph *gs[1] = {g};
+    return decode_common(gs, 1, nullptr, nullptr, syndromes, num_shots, obs_out, weight_out, status_out, stream,
+                         true);
+}
+
+}  // extern "C"

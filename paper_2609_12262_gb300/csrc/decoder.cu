@@ -1,0 +1,1051 @@
+// decoder.cu -- warp-per-shot parallel sparse-blossom decoder for sm_103a.
+//
+// One warp decodes one shot end to end (a persistent grid pulls shots from a
+// device work counter):
+//   1. defect compaction: the shot's syndrome bitmap is read with 16-byte
+//      vector loads and compacted by a warp prefix sum (input D of the paper's
+//      "Decoding task"; Alg. 1 input).
+//   2. flooder: every detection event s owns an explored ball {x : dist(s,x) <=
+//      R_s} with exact graph distances (hash table keyed by (vertex, event)).
+//      A ball is grown band by band (R -> R + band, band >= largest weight) by
+//      warp-parallel label-correcting relaxation from the previous band; each
+//      new vertex is checked against the other events' balls at itself and at
+//      its neighbours, which records the exact distance of every pair of
+//      events whose balls touch.  The graph-fill region of s (SI S1) is the
+//      ball of radius Rad(s) <= R_s, so two regions are found touching exactly
+//      when their pair distance equals Rad(a) + Rad(b) (ARRIVE = a band
+//      extension, COLLIDE = a tight pair, boundary COLLIDE = Rad(s) reaching
+//      the nearest boundary, IMPLODE = an inner blossom's dual reaching 0).
+//   3. Algorithm 1, level 1: balls of radius b_1/2 give every pair within b_1
+//      and every boundary contact; union-find links, diameter <= d_1 and the
+//      parity condition decide the level-1 processing clusters.
+//   4. Algorithm 2: level-1 clusters are solved independently (closed form for
+//      the isolated pair and boundary singleton, the event loop otherwise), then
+//      every remaining event runs from t = 0 with the stopped level-1
+//      configurations present as frozen regions (hierarchical execution rule).
+//   5. Tracing: blossoms are expanded into matched event pairs and boundary
+//      matches; the weight is the sum of the tight pair / boundary distances and
+//      the observable mask the XOR of the canonical paths' masks.
+//
+// Simultaneous events are applied in the canonical order (t, kind, lo, hi) with
+// kind EXTEND < IMPLODE < COLLIDE < BOUNDARY and lo, hi the ranks of the events
+// in the sorted defect list, which makes the result independent of execution
+// order and equal to global sparse blossom (Theorem 1).
+//
+// Every loop is bounded: the event budget, hash probe lengths and list
+// capacities end a shot with a status code instead of spinning.
+
+#include <climits>
+#include <cstdint>
+
+#include "qec_internal.h"
+
+#define WS 32   // lanes per warp
+
+namespace qec {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned long long EMPTY64 = ~0ull;
+constexpr int INF32 = INT_MAX;
+
+enum { EV_EXTEND = 0, EV_IMPLODE = 1, EV_COLLIDE = 2, EV_BOUNDARY = 3 };
+constexpr int ID_BITS = 18;
+constexpr int ID_MAX = (1 << ID_BITS) - 1;
+constexpr long long T_MAX = (1LL << 26) - 1;
+
+enum { MATE_NONE = -1, MATE_BOUNDARY = -2 };
+
+// slab counters
+enum { C_ECOUNT = 0, C_WL = 1, C_NPAIRS = 2, C_CCOUNT = 3, C_NFREE = 4, C_ERR = 5, C_HFILL = 6, C_NHI = 7,
+       C_TOTAL = 16 };
+enum { ERR_CAP = 1, ERR_INTERNAL = 2 };
+
+__device__ __forceinline__ unsigned long long ev_key(long long t, int kind, int lo, int hi) {
+    t = t < T_MAX ? t : T_MAX;
+    return ((unsigned long long)t << 38) | ((unsigned long long)kind << 36) |
+           ((unsigned long long)lo << 18) | (unsigned long long)hi;
+}
+
+__device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
+#pragma unroll
+    for (int o = WS / 2; o; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(FULL, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum64(long long v) {
+#pragma unroll
+    for (int o = WS / 2; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+struct Slab {
+    // per detection event (source)
+    int *svtx, *srad, *stop, *sR, *sbeg, *scnt, *sexh, *inplay, *comp, *cst0, *cst1, *cst2;
+    unsigned long long *sbnd;
+    // explored entries: key (vertex << 32 | source), value exact distance
+    unsigned long long *hkey;
+    int *hval;
+    int *ent, *wl0, *wl1;
+    // pairs: key (lo << 32 | hi), value distance, list of used slots
+    unsigned long long *pkey;
+    int *pval, *plist;
+    // matcher nodes (leaf s = node s, blossoms above K)
+    int *y, *bpar, *label, *tpar, *tps, *tpo, *mate, *ms, *mo, *nroot, *minleaf, *cbeg, *clen,
+        *alive, *freel, *tmpa, *tmpb, *stk;
+    int *cnode, *cs, *co;
+    int *ctr;
+};
+
+template <typename T>
+__host__ __device__ inline T *bump(char *&p, long long n) {
+    uintptr_t q = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+    T *r = reinterpret_cast<T *>(q);
+    p = reinterpret_cast<char *>(q + sizeof(T) * (size_t)n);
+    return r;
+}
+
+__host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &S) {
+    char *p = base;
+    S.svtx = bump<int>(p, c.kc); S.srad = bump<int>(p, c.kc); S.stop = bump<int>(p, c.kc);
+    S.sR = bump<int>(p, c.kc); S.sbeg = bump<int>(p, c.kc); S.scnt = bump<int>(p, c.kc);
+    S.sexh = bump<int>(p, c.kc); S.inplay = bump<int>(p, c.kc); S.comp = bump<int>(p, c.kc);
+    S.cst0 = bump<int>(p, c.kc); S.cst1 = bump<int>(p, c.kc); S.cst2 = bump<int>(p, c.kc);
+    S.sbnd = bump<unsigned long long>(p, c.kc);
+    S.hkey = bump<unsigned long long>(p, c.hc); S.hval = bump<int>(p, c.hc);
+    S.ent = bump<int>(p, c.ec); S.wl0 = bump<int>(p, c.wc); S.wl1 = bump<int>(p, c.wc);
+    S.pkey = bump<unsigned long long>(p, c.phc); S.pval = bump<int>(p, c.phc); S.plist = bump<int>(p, c.phc);
+    S.y = bump<int>(p, c.nc); S.bpar = bump<int>(p, c.nc); S.label = bump<int>(p, c.nc);
+    S.tpar = bump<int>(p, c.nc); S.tps = bump<int>(p, c.nc); S.tpo = bump<int>(p, c.nc);
+    S.mate = bump<int>(p, c.nc); S.ms = bump<int>(p, c.nc); S.mo = bump<int>(p, c.nc);
+    S.nroot = bump<int>(p, c.nc); S.minleaf = bump<int>(p, c.nc); S.cbeg = bump<int>(p, c.nc);
+    S.clen = bump<int>(p, c.nc); S.alive = bump<int>(p, c.nc); S.freel = bump<int>(p, c.nc);
+    S.tmpa = bump<int>(p, 2 * c.nc + 64); S.tmpb = bump<int>(p, 2 * c.nc + 64);
+    S.stk = bump<int>(p, 4 * c.nc + 64);
+    S.cnode = bump<int>(p, c.cc); S.cs = bump<int>(p, c.cc); S.co = bump<int>(p, c.cc);
+    S.ctr = bump<int>(p, C_TOTAL);
+    return (long long)(p - base) + 16;
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct Shot {
+    unsigned long long deadline;   // globaltimer value after which the shot gives up (0 = none)
+    DGraph g;
+    int K;            // detection events
+    unsigned hmask;   // explored-entry hash mask
+    unsigned pmask;   // pair hash mask
+    int ec, wc, nc, cc;
+    int band;
+    long long t;
+    long long events;
+    long long max_events;
+};
+
+__device__ __forceinline__ unsigned hslot(int v, unsigned mask) {
+    return ((unsigned)v * 2654435761u) & mask;
+}
+
+__device__ __forceinline__ unsigned pslot(int lo, int hi, unsigned mask) {
+    return (((unsigned)lo * 2654435761u) ^ ((unsigned)hi * 2246822519u)) & mask;
+}
+
+__device__ __forceinline__ void set_err(const Slab &S, int bit) { atomicOr(&S.ctr[C_ERR], bit); }
+
+// exact distance of (v, s) if explored, else INF32
+__device__ int ht_get(const Slab &S, const Shot &C, int v, int s) {
+    const unsigned long long key = ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
+    unsigned i = hslot(v, C.hmask);
+    for (unsigned n = 0; n <= C.hmask; n++) {
+        unsigned long long k = __ldcg(&S.hkey[i]);
+        if (k == key) return __ldcg(&S.hval[i]);
+        if (k == EMPTY64) return INF32;
+        i = (i + 1) & C.hmask;
+    }
+    return INF32;
+}
+
+// insert-or-decrease; returns 1 inserted, 2 decreased, 0 unchanged, -1 table full
+__device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d) {
+    const unsigned long long key = ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
+    unsigned i = hslot(v, C.hmask);
+    for (unsigned n = 0; n <= C.hmask; n++) {
+        unsigned long long k = __ldcg(&S.hkey[i]);
+        if (k == EMPTY64) {
+            unsigned long long prev = atomicCAS(&S.hkey[i], EMPTY64, key);
+            if (prev == EMPTY64) {
+                atomicMin(&S.hval[i], d);
+                int f = atomicAdd(&S.ctr[C_HFILL], 1);
+                if ((unsigned)f * 2u > C.hmask) set_err(S, ERR_CAP);
+                return 1;
+            }
+            k = prev;
+        }
+        if (k == key) {
+            int old = atomicMin(&S.hval[i], d);
+            return d < old ? 2 : 0;
+        }
+        i = (i + 1) & C.hmask;
+    }
+    set_err(S, ERR_CAP);
+    return -1;
+}
+
+__device__ void pair_upsert(const Slab &S, const Shot &C, int a, int b, int d) {
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    const unsigned long long key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
+    unsigned i = pslot(lo, hi, C.pmask);
+    for (unsigned n = 0; n <= C.pmask; n++) {
+        unsigned long long k = __ldcg(&S.pkey[i]);
+        if (k == EMPTY64) {
+            unsigned long long prev = atomicCAS(&S.pkey[i], EMPTY64, key);
+            if (prev == EMPTY64) {
+                atomicMin(&S.pval[i], d);
+                int idx = atomicAdd(&S.ctr[C_NPAIRS], 1);
+                if ((unsigned)idx * 2u > C.pmask) set_err(S, ERR_CAP);
+                else S.plist[idx] = (int)i;
+                return;
+            }
+            k = prev;
+        }
+        if (k == key) {
+            atomicMin(&S.pval[i], d);
+            return;
+        }
+        i = (i + 1) & C.pmask;
+    }
+    set_err(S, ERR_CAP);
+}
+
+__device__ int pair_get(const Slab &S, const Shot &C, int a, int b) {
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    const unsigned long long key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
+    unsigned i = pslot(lo, hi, C.pmask);
+    for (unsigned n = 0; n <= C.pmask; n++) {
+        unsigned long long k = __ldcg(&S.pkey[i]);
+        if (k == key) return __ldcg(&S.pval[i]);
+        if (k == EMPTY64) return INF32;
+        i = (i + 1) & C.pmask;
+    }
+    return INF32;
+}
+
+__device__ __forceinline__ Slot load_slot(const DGraph &g, int j) {
+    int4 v = __ldg(reinterpret_cast<const int4 *>(g.slot) + j);
+    Slot s;
+    s.nbr = v.x; s.w = v.y; s.eid = v.z; s.pad = v.w;
+    return s;
+}
+
+// Record every pair (s, s') whose balls meet at vertex z: `base` is the
+// distance from s to z through the edge being examined.
+__device__ void contacts_at(const Slab &S, const Shot &C, int s, int z, int base) {
+    unsigned i = hslot(z, C.hmask);
+    for (unsigned n = 0; n <= C.hmask; n++) {
+        unsigned long long k = __ldcg(&S.hkey[i]);
+        if (k == EMPTY64) return;
+        if ((int)(k >> 32) == z) {
+            int s2 = (int)(unsigned)(k & 0xffffffffu);
+            if (s2 != s) pair_upsert(S, C, s, s2, base + __ldcg(&S.hval[i]));
+        }
+        i = (i + 1) & C.hmask;
+    }
+}
+
+__device__ __forceinline__ void bnd_update(const Slab &S, int s, int d, int eid) {
+    unsigned long long v = ((unsigned long long)(unsigned)d << 32) | (unsigned)eid;
+    atomicMin(&S.sbnd[s], v);
+}
+
+// Grow the explored ball of source s from radius sR[s] to Rn (Rn - sR[s] >= wmax).
+// All lanes call; warp-uniform.
+__device__ void extend(const Slab &S, const Shot &C, int s, int Rn, int lane) {
+    const DGraph &g = C.g;
+    const int fb = S.sbeg[s], fc = S.scnt[s];
+    const int band_beg = __ldcg(&S.ctr[C_ECOUNT]);
+    const int *F = S.ent + fb;
+    int nf = fc;
+    int *Wn = S.wl0, *Wo = S.wl1;
+    for (int iter = 0;; iter++) {
+        if (iter >= 4096) { if (lane == 0) set_err(S, ERR_INTERNAL); break; }
+        __syncwarp();
+        if (lane == 0) S.ctr[C_WL] = 0;
+        __syncwarp();
+        for (int i = lane; i < nf; i += WS) {
+            const int x = F[i];
+            const int dx = ht_get(S, C, x, s);
+            const int r0 = __ldg(g.row + x), r1 = __ldg(g.row + x + 1);
+            for (int j = r0; j < r1; j++) {
+                Slot sl = load_slot(g, j);
+                const int nd = dx + sl.w;
+                if (sl.nbr < 0) { bnd_update(S, s, nd, sl.eid); continue; }
+                if (nd > Rn) continue;
+                int r = ht_upsert(S, C, sl.nbr, s, nd);
+                if (r == 1) {
+                    int e = atomicAdd(&S.ctr[C_ECOUNT], 1);
+                    if (e < C.ec) S.ent[e] = sl.nbr; else set_err(S, ERR_CAP);
+                }
+                if (r >= 1) {
+                    int w = atomicAdd(&S.ctr[C_WL], 1);
+                    if (w < C.wc) Wn[w] = sl.nbr; else set_err(S, ERR_CAP);
+                }
+            }
+        }
+        __syncwarp();
+        int nw = __ldcg(&S.ctr[C_WL]);
+        int err = __ldcg(&S.ctr[C_ERR]);
+        if (nw == 0 || err) break;
+        F = Wn;
+        nf = nw;
+        int *t = Wn; Wn = Wo; Wo = t;
+    }
+    __syncwarp();
+    const int band_end = min(__ldcg(&S.ctr[C_ECOUNT]), C.ec);
+    if (lane == 0) {
+        S.sR[s] = Rn;
+        S.sbeg[s] = band_beg;
+        S.scnt[s] = band_end - band_beg;
+        if (band_end == band_beg) S.sexh[s] = 1;
+    }
+    for (int i = band_beg + lane; i < band_end; i += WS) {
+        const int yv = S.ent[i];
+        const int dy = ht_get(S, C, yv, s);
+        contacts_at(S, C, s, yv, dy);
+        const int r0 = __ldg(g.row + yv), r1 = __ldg(g.row + yv + 1);
+        for (int j = r0; j < r1; j++) {
+            Slot sl = load_slot(g, j);
+            if (sl.nbr >= 0) contacts_at(S, C, s, sl.nbr, dy + sl.w);
+        }
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- matcher --
+
+// Child of blossom B that contains `leaf` (-1 if B is not an ancestor).
+__device__ __forceinline__ int child_of(const Slab &S, int B, int leaf) {
+    int v = leaf;
+    for (int n = 0; n < 1 << 20 && v >= 0 && S.bpar[v] != B; n++) v = S.bpar[v];
+    return v;
+}
+
+// flip matches along the tree path from outer A to its root (lane 0)
+__device__ void flip_to_root(const Slab &S, int A) {
+    int v = A;
+    for (int n = 0; n < 1 << 22 && S.tpar[v] >= 0; n++) {
+        const int I = S.tpar[v];
+        const int O = S.tpar[I];
+        if (O < 0) { S.ctr[C_ERR] |= ERR_INTERNAL; return; }
+        S.mate[I] = O; S.ms[I] = S.tps[I]; S.mo[I] = S.tpo[I];
+        S.mate[O] = I; S.ms[O] = S.tpo[I]; S.mo[O] = S.tps[I];
+        v = O;
+    }
+}
+
+// Events (b), (f), (g).  B < 0: boundary.  All lanes call.
+__device__ void ev_augment(const Slab &S, Shot &C, int A, int a, int B, int b, int lane, int nhi) {
+    int rA = 0, rB = -3;
+    if (lane == 0) {
+        rA = S.nroot[A];
+        const bool bout = B >= 0 && S.label[B] == 1;
+        rB = bout ? S.nroot[B] : -3;
+        flip_to_root(S, A);
+        if (bout) flip_to_root(S, B);
+        if (B >= 0) {
+            S.mate[A] = B; S.ms[A] = a; S.mo[A] = b;
+            S.mate[B] = A; S.ms[B] = b; S.mo[B] = a;
+        } else {
+            S.mate[A] = MATE_BOUNDARY; S.ms[A] = a; S.mo[A] = -1;
+        }
+    }
+    rA = __shfl_sync(FULL, rA, 0);
+    rB = __shfl_sync(FULL, rB, 0);
+    __syncwarp();
+    for (int v = lane; v < nhi; v += WS) {
+        if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0 && (S.nroot[v] == rA || S.nroot[v] == rB)) {
+            S.label[v] = 0; S.tpar[v] = -1; S.nroot[v] = -1;
+        }
+    }
+    __syncwarp();
+}
+
+// Event (a): outer A touches frozen B (matched to C).  Lane 0 only.
+__device__ void ev_grow(const Slab &S, int A, int a, int B, int b) {
+    const int Cn = S.mate[B];
+    S.label[B] = -1; S.tpar[B] = A; S.tps[B] = b; S.tpo[B] = a; S.nroot[B] = S.nroot[A];
+    S.label[Cn] = 1; S.tpar[Cn] = B; S.tps[Cn] = S.ms[Cn]; S.tpo[Cn] = S.mo[Cn]; S.nroot[Cn] = S.nroot[A];
+}
+
+// Event (c): outer A, B in one tree form a blossom.  All lanes call.
+__device__ void ev_blossom(const Slab &S, Shot &C, int A, int a, int B, int b, int lane, int &nhi) {
+    int N = -1, L = -1, Lroot = 0;
+    if (lane == 0) {
+        int na = 0, nb = 0;
+        for (int v = A; v >= 0 && na < 2 * C.nc; v = S.tpar[v]) S.tmpa[na++] = v;
+        for (int v = B; v >= 0 && nb < 2 * C.nc; v = S.tpar[v]) S.tmpb[nb++] = v;
+        while (na > 1 && nb > 1 && S.tmpa[na - 2] == S.tmpb[nb - 2]) { na--; nb--; }
+        L = S.tmpa[na - 1];
+        const int m = na + nb - 1;
+        const int nf = S.ctr[C_NFREE];
+        const int cb = S.ctr[C_CCOUNT];
+        if (L != S.tmpb[nb - 1] || nf <= 0 || cb + m > C.cc) {
+            S.ctr[C_ERR] |= (L != S.tmpb[nb - 1]) ? ERR_INTERNAL : ERR_CAP;
+        } else {
+            N = S.freel[nf - 1];
+            S.ctr[C_NFREE] = nf - 1;
+            S.ctr[C_CCOUNT] = cb + m;
+            int i = 0;
+            S.cnode[cb + i++] = L;
+            for (int j = na - 2; j >= 0; j--) S.cnode[cb + i++] = S.tmpa[j];
+            for (int j = 0; j <= nb - 2; j++) S.cnode[cb + i++] = S.tmpb[j];
+            const int ia = na - 1;
+            int ml = INT_MAX;
+            for (int j = 0; j < m; j++) {
+                const int x = S.cnode[cb + j], z = S.cnode[cb + (j + 1) % m];
+                if (j < ia) { S.cs[cb + j] = S.tpo[z]; S.co[cb + j] = S.tps[z]; }
+                else if (j == ia) { S.cs[cb + j] = a; S.co[cb + j] = b; }
+                else { S.cs[cb + j] = S.tps[x]; S.co[cb + j] = S.tpo[x]; }
+                ml = min(ml, S.minleaf[x]);
+            }
+            S.alive[N] = 1; S.y[N] = 0; S.bpar[N] = -1; S.label[N] = 1;
+            S.tpar[N] = S.tpar[L]; S.tps[N] = S.tps[L]; S.tpo[N] = S.tpo[L];
+            S.mate[N] = S.mate[L]; S.ms[N] = S.ms[L]; S.mo[N] = S.mo[L];
+            Lroot = (S.nroot[L] == L);
+            S.nroot[N] = Lroot ? N : S.nroot[L];
+            S.minleaf[N] = ml; S.cbeg[N] = cb; S.clen[N] = m;
+            for (int j = 0; j < m; j++) S.bpar[S.cnode[cb + j]] = N;
+        }
+    }
+    N = __shfl_sync(FULL, N, 0);
+    L = __shfl_sync(FULL, L, 0);
+    Lroot = __shfl_sync(FULL, Lroot, 0);
+    __syncwarp();
+    if (N < 0) return;
+    nhi = max(nhi, N + 1);
+    for (int v = lane; v < nhi; v += WS) {
+        if (!S.alive[v] || S.bpar[v] >= 0 || v == N) continue;
+        const int tp = S.tpar[v];
+        if (tp >= 0 && S.bpar[tp] == N) S.tpar[v] = N;
+        const int mt = S.mate[v];
+        if (mt >= 0 && S.bpar[mt] == N) S.mate[v] = N;
+        if (Lroot && S.nroot[v] == L) S.nroot[v] = N;
+    }
+    for (int s = lane; s < C.K; s += WS) {
+        const int tp = S.stop[s];
+        if (tp != N && S.bpar[tp] == N) S.stop[s] = N;
+    }
+    __syncwarp();
+}
+
+// Event (d): inner blossom B with zero dual shatters.  All lanes call.
+__device__ void ev_shatter(const Slab &S, Shot &C, int B, int lane) {
+    for (int s = lane; s < C.K; s += WS)
+        if (S.stop[s] == B) {
+            const int c = child_of(S, B, s);
+            if (c >= 0) S.stop[s] = c; else atomicOr(&S.ctr[C_ERR], ERR_INTERNAL);
+        }
+    __syncwarp();
+    if (lane == 0) {
+        const int m = S.clen[B], cb = S.cbeg[B];
+        const int P = S.tpar[B], Cn = S.mate[B];
+        const int xp = S.tps[B] >= 0 ? child_of(S, B, S.tps[B]) : -1;
+        const int xc = S.ms[B] >= 0 ? child_of(S, B, S.ms[B]) : -1;
+        int ip = -1, ic = -1;
+        for (int j = 0; j < m; j++) {
+            if (S.cnode[cb + j] == xp) ip = j;
+            if (S.cnode[cb + j] == xc) ic = j;
+        }
+        if (ip < 0 || ic < 0 || Cn < 0) {
+            S.ctr[C_ERR] |= ERR_INTERNAL;
+        } else {
+            const int rootB = S.nroot[B];
+            for (int j = 0; j < m; j++) S.bpar[S.cnode[cb + j]] = -1;
+            const int fwd = ((ic - ip) % m + m) % m;
+            const int dir = (fwd % 2 == 0) ? 1 : -1;
+            const int L = dir > 0 ? fwd : m - fwd;
+            int prev = -1;
+            for (int j = 0; j <= L; j++) {
+                const int idx = ((ip + dir * j) % m + m) % m;
+                const int q = S.cnode[cb + idx];
+                S.label[q] = (j % 2 == 0) ? -1 : 1;
+                S.nroot[q] = rootB;
+                if (j == 0) {
+                    S.tpar[q] = P; S.tps[q] = S.tps[B]; S.tpo[q] = S.tpo[B];
+                } else {
+                    const int pidx = ((ip + dir * (j - 1)) % m + m) % m;
+                    int self, other;
+                    if (dir > 0) { self = S.co[cb + pidx]; other = S.cs[cb + pidx]; }
+                    else { self = S.cs[cb + idx]; other = S.co[cb + idx]; }
+                    S.tpar[q] = prev; S.tps[q] = self; S.tpo[q] = other;
+                    if (j % 2 == 1) {
+                        S.mate[q] = prev; S.ms[q] = self; S.mo[q] = other;
+                        S.mate[prev] = q; S.ms[prev] = other; S.mo[prev] = self;
+                    }
+                }
+                prev = q;
+            }
+            const int qL = prev;
+            S.mate[qL] = Cn; S.ms[qL] = S.ms[B]; S.mo[qL] = S.mo[B];
+            S.mate[Cn] = qL; S.tpar[Cn] = qL;
+            const int rem = m - 1 - L;
+            for (int j = 1; j <= rem; j += 2) {
+                const int i1 = ((ic + dir * j) % m + m) % m;
+                const int i2 = ((ic + dir * (j + 1)) % m + m) % m;
+                const int x = S.cnode[cb + i1], z = S.cnode[cb + i2];
+                int lx, lz;
+                if (dir > 0) { lx = S.cs[cb + i1]; lz = S.co[cb + i1]; }
+                else { lx = S.co[cb + i2]; lz = S.cs[cb + i2]; }
+                S.label[x] = 0; S.label[z] = 0;
+                S.tpar[x] = -1; S.tpar[z] = -1;
+                S.nroot[x] = -1; S.nroot[z] = -1;
+                S.mate[x] = z; S.ms[x] = lx; S.mo[x] = lz;
+                S.mate[z] = x; S.ms[z] = lz; S.mo[z] = lx;
+            }
+            S.alive[B] = 0; S.tpar[B] = -1; S.mate[B] = MATE_NONE; S.y[B] = 0; S.clen[B] = 0;
+            const int nf = S.ctr[C_NFREE];
+            S.freel[nf] = B;
+            S.ctr[C_NFREE] = nf + 1;
+        }
+    }
+    __syncwarp();
+}
+
+// Fresh growing root for source s.
+__device__ __forceinline__ void make_root(const Slab &S, int s) {
+    S.alive[s] = 1; S.y[s] = 0; S.srad[s] = 0; S.bpar[s] = -1; S.label[s] = 1;
+    S.tpar[s] = -1; S.mate[s] = MATE_NONE; S.nroot[s] = s; S.stop[s] = s; S.inplay[s] = 1;
+}
+
+enum { RUN_OK = 0, RUN_NOSOL = 1, RUN_BUDGET = 2, RUN_CAP = 3, RUN_INTERNAL = 4 };
+
+// Event loop over the sources with inplay[s] = 1, from t = 0 (SI S1).
+__device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
+    C.t = 0;
+    for (;;) {
+        if (++C.events > C.max_events) return RUN_BUDGET;
+        if (C.deadline && (C.events & 63) == 0) {
+            bool late = false;
+            if (lane == 0) late = now_ns() > C.deadline;
+            if (__shfl_sync(FULL, late, 0)) return RUN_BUDGET;
+        }
+        unsigned long long best = EMPTY64;
+        bool outer = false, bad = false;
+        int inner_leaf_min = INT_MAX;
+        for (int s = lane; s < C.K; s += WS) {
+            if (!S.inplay[s]) continue;
+            const int A = S.stop[s];
+            const int lab = S.label[A];
+            if (lab == 1) {
+                outer = true;
+                const int rad = S.srad[s];
+                if (!S.sexh[s]) {
+                    // due when Rad(s) reaches R_s + 1; several regions can reach it at
+                    // the same instant and are extended one after another at that time
+                    const int ahead = S.sR[s] + 1 - rad;
+                    if (ahead < 0) bad = true;
+                    best = min(best, ev_key(C.t + ahead, EV_EXTEND, s, 0));
+                }
+                const unsigned long long bb = __ldcg(&S.sbnd[s]);
+                if (bb != EMPTY64) {
+                    const int bd = (int)(bb >> 32);
+                    if (bd < rad) bad = true;
+                    else best = min(best, ev_key(C.t + (bd - rad), EV_BOUNDARY, s, ID_MAX));
+                }
+            } else if (lab == -1 && A == s) {
+                inner_leaf_min = min(inner_leaf_min, S.y[s]);
+            }
+        }
+        const int np = __ldcg(&S.ctr[C_NPAIRS]);
+        for (int i = lane; i < np; i += WS) {
+            const int sl = S.plist[i];
+            const unsigned long long k = __ldcg(&S.pkey[sl]);
+            const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
+            if (!S.inplay[a] || !S.inplay[b]) continue;
+            const int A = S.stop[a], B = S.stop[b];
+            if (A == B) continue;
+            const int r = S.label[A] + S.label[B];
+            if (r <= 0) continue;
+            const int gap = __ldcg(&S.pval[sl]) - S.srad[a] - S.srad[b];
+            if (gap < 0 || gap % r) { bad = true; continue; }
+            best = min(best, ev_key(C.t + gap / r, EV_COLLIDE, a, b));
+        }
+        for (int v = C.K + lane; v < nhi; v += WS) {
+            if (S.alive[v] && S.bpar[v] < 0 && S.label[v] == -1)
+                best = min(best, ev_key(C.t + S.y[v], EV_IMPLODE, S.minleaf[v], 0));
+        }
+        best = warp_min64(best);
+        outer = __any_sync(FULL, outer);
+        bad = __any_sync(FULL, bad);
+        inner_leaf_min = __reduce_min_sync(FULL, (unsigned)inner_leaf_min);
+        if (bad) return RUN_INTERNAL;
+        if (!outer) return RUN_OK;
+        if (best == EMPTY64) return RUN_NOSOL;
+        const long long tn = (long long)(best >> 38);
+        const int kind = (int)((best >> 36) & 3);
+        const int lo = (int)((best >> 18) & ID_MAX);
+        const int hi = (int)(best & ID_MAX);
+        if (tn >= T_MAX) return RUN_CAP;
+        const int dt = (int)(tn - C.t);
+        if (dt > inner_leaf_min) return RUN_INTERNAL;
+        if (dt > 0) {
+            for (int v = lane; v < nhi; v += WS)
+                if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0) S.y[v] += S.label[v] * dt;
+            for (int s = lane; s < C.K; s += WS)
+                if (S.inplay[s]) S.srad[s] += S.label[S.stop[s]] * dt;
+        }
+        C.t = tn;
+        __syncwarp();
+        if (kind == EV_EXTEND) {
+            const int s = lo;
+            extend(S, C, s, S.sR[s] + C.band, lane);
+        } else if (kind == EV_IMPLODE) {
+            ev_shatter(S, C, S.stop[lo], lane);
+        } else if (kind == EV_BOUNDARY) {
+            ev_augment(S, C, S.stop[lo], lo, -1, -1, lane, nhi);
+        } else {
+            int a = lo, b = hi;
+            int A = S.stop[a], B = S.stop[b];
+            if (S.label[A] != 1) { int t = A; A = B; B = t; t = a; a = b; b = t; }
+            const int lb = S.label[B];
+            if (lb == 1) {
+                if (S.nroot[A] == S.nroot[B]) ev_blossom(S, C, A, a, B, b, lane, nhi);
+                else ev_augment(S, C, A, a, B, b, lane, nhi);
+            } else if (lb == 0 && S.mate[B] == MATE_BOUNDARY) {
+                ev_augment(S, C, A, a, B, b, lane, nhi);
+            } else if (lb == 0 && S.mate[B] >= 0) {
+                if (lane == 0) ev_grow(S, A, a, B, b);
+                __syncwarp();
+            } else {
+                return RUN_INTERNAL;
+            }
+        }
+        const int err = __ldcg(&S.ctr[C_ERR]);
+        if (err) return (err & ERR_INTERNAL) ? RUN_INTERNAL : RUN_CAP;
+    }
+}
+
+// Canonical path observable from source s (its Dijkstra tree) to vertex x at
+// distance dx: predecessor = lowest edge id among tight edges.  All lanes call.
+__device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int dx, int lane) {
+    const DGraph &g = C.g;
+    for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s]; n++) extend(S, C, s, S.sR[s] + C.band, lane);
+    unsigned long long o = 0;
+    const int src = S.svtx[s];
+    int cur = x, dcur = dx;
+    for (int n = 0; n < 1 << 22 && cur != src; n++) {
+        const int r0 = __ldg(g.row + cur), r1 = __ldg(g.row + cur + 1);
+        unsigned long long best = EMPTY64;
+        for (int j = r0 + lane; j < r1; j += WS) {
+            Slot sl = load_slot(g, j);
+            if (sl.nbr < 0) continue;
+            const int dy = ht_get(S, C, sl.nbr, s);
+            if (dy != INF32 && dy + sl.w == dcur)
+                best = min(best, ((unsigned long long)(unsigned)sl.eid << 32) | (unsigned)sl.nbr);
+        }
+        best = warp_min64(best);
+        if (best == EMPTY64) { if (lane == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
+        const int e = (int)(best >> 32);
+        o ^= __ldg(g.eobs + e);
+        cur = (int)(unsigned)(best & 0xffffffffu);
+        dcur = ht_get(S, C, cur, s);
+    }
+    return o;
+}
+
+// Expand the final matching into leaf-level pairs (tmpa[i], tmpb[i]; tmpb = -1
+// for a boundary match) and accumulate weight (internal units) and obs.
+__device__ void trace(const Slab &S, Shot &C, int lane, int nhi, long long &wint, unsigned long long &obs) {
+    int np = 0;
+    if (lane == 0) {
+        int *stk = S.stk;
+        const int stk_cap = 4 * C.nc + 60;
+        for (int v = 0; v < nhi; v++) {
+            if (!S.alive[v] || S.bpar[v] >= 0) continue;
+            const int mt = S.mate[v];
+            int sp = 0;
+            if (mt == MATE_BOUNDARY) {
+                S.tmpa[np] = S.ms[v]; S.tmpb[np] = -1; np++;
+            } else if (mt >= 0 && v < mt) {
+                S.tmpa[np] = S.ms[v]; S.tmpb[np] = S.mo[v]; np++;
+                stk[sp++] = mt; stk[sp++] = S.mo[v];
+            } else {
+                continue;
+            }
+            stk[sp++] = v; stk[sp++] = S.ms[v];
+            while (sp > 0) {
+                const int ext = stk[--sp];
+                const int node = stk[--sp];
+                if (node < C.K) continue;
+                const int m = S.clen[node], cb = S.cbeg[node];
+                const int c0 = ext >= 0 ? child_of(S, node, ext) : -1;
+                if (c0 < 0 || m <= 0) { S.ctr[C_ERR] |= ERR_INTERNAL; break; }
+                int i0 = 0;
+                for (int j = 0; j < m; j++) if (S.cnode[cb + j] == c0) i0 = j;
+                if (sp + 2 * m + 2 > stk_cap || np + m > 2 * C.nc) { S.ctr[C_ERR] |= ERR_CAP; break; }
+                stk[sp++] = c0; stk[sp++] = ext;
+                for (int j = 1; j < m; j += 2) {
+                    const int i1 = (i0 + j) % m, i2 = (i0 + j + 1) % m;
+                    const int lx = S.cs[cb + i1], lz = S.co[cb + i1];
+                    S.tmpa[np] = lx; S.tmpb[np] = lz; np++;
+                    stk[sp++] = S.cnode[cb + i1]; stk[sp++] = lx;
+                    stk[sp++] = S.cnode[cb + i2]; stk[sp++] = lz;
+                }
+            }
+        }
+    }
+    np = __shfl_sync(FULL, np, 0);
+    __syncwarp();
+    long long w = 0;
+    unsigned long long o = 0;
+    for (int i = lane; i < np; i += WS) {
+        const int a = S.tmpa[i], b = S.tmpb[i];
+        if (a < 0 || a >= C.K || b >= C.K) { set_err(S, ERR_INTERNAL); continue; }
+        if (b < 0) {
+            const unsigned long long bb = __ldcg(&S.sbnd[a]);
+            if (bb == EMPTY64) { set_err(S, ERR_INTERNAL); continue; }
+            w += (long long)(bb >> 32);
+            o ^= __ldg(C.g.eobs + (int)(unsigned)(bb & 0xffffffffu));
+        } else {
+            const int d = pair_get(S, C, a, b);
+            if (d == INF32) { set_err(S, ERR_INTERNAL); continue; }
+            w += d;
+        }
+    }
+    w = warp_sum64(w);
+#pragma unroll
+    for (int off = WS / 2; off; off >>= 1) o ^= __shfl_xor_sync(FULL, o, off);
+    if (C.g.internal_obs && !__ldcg(&S.ctr[C_ERR])) {
+        // detector-detector edges carry observables: walk the canonical paths
+        for (int i = 0; i < np; i++) {
+            const int a = S.tmpa[i], b = S.tmpb[i];
+            if (b < 0) {
+                const unsigned long long bb = __ldcg(&S.sbnd[a]);
+                const int e = (int)(unsigned)(bb & 0xffffffffu);
+                const int2 ue = __ldg(C.g.eend + e);
+                o ^= path_obs(S, C, a, ue.x, (int)(bb >> 32) - ue.y, lane);
+            } else {
+                const int lo = min(a, b), hi = max(a, b);
+                o ^= path_obs(S, C, lo, S.svtx[hi], pair_get(S, C, lo, hi), lane);
+            }
+        }
+    }
+    wint = w;
+    obs = o;
+}
+
+__device__ void clear_tables(const Slab &S, const Shot &C, int lane) {
+    for (unsigned i = lane; i <= C.hmask; i += WS) { S.hkey[i] = EMPTY64; S.hval[i] = INF32; }
+    for (unsigned i = lane; i <= C.pmask; i += WS) { S.pkey[i] = EMPTY64; S.pval[i] = INF32; }
+    for (int i = lane; i < C_TOTAL; i += WS) S.ctr[i] = 0;
+    __syncwarp();
+}
+
+__device__ __forceinline__ unsigned next_pow2(unsigned x) {
+    x--; x |= x >> 1; x |= x >> 2; x |= x >> 4; x |= x >> 8; x |= x >> 16;
+    return x + 1;
+}
+
+// Compact the set bits of the shot's syndrome row into S.svtx; returns K
+// (or -1 when K exceeds kcap).
+__device__ int load_defects(const Slab &S, const DGraph &g, const unsigned *row, int kcap, int lane) {
+    int K = 0;
+    const int nvec = g.words >> 2;
+    const uint4 *rv = reinterpret_cast<const uint4 *>(row);
+    for (int base = 0; base < nvec; base += WS) {
+        const int i = base + lane;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (i < nvec) v = __ldg(rv + i);
+        unsigned wv[4] = {v.x, v.y, v.z, v.w};
+        // drop padding bits beyond n
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int bit0 = (i * 4 + q) * 32;
+            if (bit0 >= g.n) wv[q] = 0;
+            else if (bit0 + 32 > g.n) wv[q] &= (1u << (g.n - bit0)) - 1u;
+        }
+        int c = __popc(wv[0]) + __popc(wv[1]) + __popc(wv[2]) + __popc(wv[3]);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < WS; o <<= 1) {
+            int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(FULL, incl, WS - 1);
+        int pos = K + incl - c;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            unsigned bits = wv[q];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (pos < kcap) S.svtx[pos] = (i * 4 + q) * 32 + b;
+                pos++;
+            }
+        }
+        K += total;
+    }
+    __syncwarp();
+    return K > kcap ? -1 : K;
+}
+
+// Decode one shot with hash tables scaled by `scale`; returns QEC_SHOT_* or -1
+// when the working set overflowed (retry with a larger scale).
+__device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
+                              int lane, unsigned scale, unsigned long long deadline, long long &w_out,
+                              unsigned long long &o_out) {
+    Shot C;
+    C.g = g;
+    C.ec = A.caps.ec; C.wc = A.caps.wc; C.nc = A.caps.nc; C.cc = A.caps.cc;
+    C.band = max(g.wmax, 1) * max(A.band_factor, 1);
+    C.events = 0;
+    C.t = 0;
+    C.deadline = deadline;
+    const int K = load_defects(S, g, row, A.caps.kc, lane);
+    if (K < 0) return -2;
+    C.K = K;
+    C.max_events = min(A.max_events, 256LL * K + 4096);
+    if (K == 0) { w_out = 0; o_out = 0; return QEC_SHOT_OK; }
+    if (K > ID_MAX - 1 || 2 * K + 8 > C.nc) return -2;
+    const unsigned hs = min(next_pow2(max(256u, 64u * (unsigned)K * scale)), (unsigned)A.caps.hc);
+    const unsigned ps = min(next_pow2(max(64u, 16u * (unsigned)K * scale)), (unsigned)A.caps.phc);
+    C.hmask = hs - 1;
+    C.pmask = ps - 1;
+    clear_tables(S, C, lane);
+    // sources, leaf nodes, free list
+    int nhi = K;
+    for (int s = lane; s < K; s += WS) {
+        S.srad[s] = 0; S.sR[s] = 0; S.scnt[s] = 1; S.sbeg[s] = s; S.sexh[s] = 0; S.inplay[s] = 0;
+        S.sbnd[s] = EMPTY64; S.ent[s] = S.svtx[s];
+        S.alive[s] = 0; S.y[s] = 0; S.bpar[s] = -1; S.label[s] = 0; S.tpar[s] = -1;
+        S.mate[s] = MATE_NONE; S.nroot[s] = -1; S.stop[s] = s; S.minleaf[s] = s; S.clen[s] = 0;
+    }
+    const int nfree = C.nc - K;
+    for (int i = lane; i < nfree; i += WS) {
+        const int v = C.nc - 1 - i;   // pop order: K, K+1, ...
+        S.freel[i] = v;
+        S.alive[v] = 0; S.clen[v] = 0; S.bpar[v] = -1;
+    }
+    if (lane == 0) { S.ctr[C_ECOUNT] = K; S.ctr[C_NFREE] = nfree; }
+    __syncwarp();
+    for (int s = lane; s < K; s += WS) {
+        int f = ht_upsert(S, C, S.svtx[s], s, 0);
+        (void)f;
+    }
+    __syncwarp();
+    // contacts between adjacent sources at t = 0
+    for (int s = lane; s < K; s += WS) {
+        const int v = S.svtx[s];
+        const int r0 = __ldg(g.row + v), r1 = __ldg(g.row + v + 1);
+        for (int j = r0; j < r1; j++) {
+            Slot sl = load_slot(g, j);
+            if (sl.nbr >= 0) contacts_at(S, C, s, sl.nbr, sl.w);
+        }
+    }
+    __syncwarp();
+    // ---- Algorithm 1, level 1: balls of radius max(b1/2, band) around every event
+    const int R1 = max(g.b1 / 2, C.band);
+    for (int s = 0; s < K; s++) {
+        extend(S, C, s, R1, lane);
+        if (__ldcg(&S.ctr[C_ERR])) break;
+    }
+    {
+        const int err = __ldcg(&S.ctr[C_ERR]);
+        if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
+    }
+    const int npairs = __ldcg(&S.ctr[C_NPAIRS]);
+    if (lane == 0) {
+        for (int s = 0; s < K; s++) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
+        for (int i = 0; i < npairs; i++) {
+            const int sl = S.plist[i];
+            if (S.pval[sl] > g.b1) continue;
+            const unsigned long long k = S.pkey[sl];
+            int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
+            while (S.comp[a] != a) a = S.comp[a];
+            while (S.comp[b] != b) b = S.comp[b];
+            if (a != b) { if (a < b) S.comp[b] = a; else S.comp[a] = b; }
+        }
+        for (int s = 0; s < K; s++) {
+            int r = s;
+            while (S.comp[r] != r) r = S.comp[r];
+            S.comp[s] = r;
+            S.cst0[r]++;
+            const unsigned long long bb = S.sbnd[s];
+            if (bb != EMPTY64 && 2LL * (long long)(bb >> 32) <= (long long)g.b1) S.cst1[r] = 1;
+        }
+        for (int i = 0; i < npairs; i++) {
+            const int sl = S.plist[i];
+            if (S.pval[sl] > g.d1) continue;
+            const unsigned long long k = S.pkey[sl];
+            const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
+            if (S.comp[a] == S.comp[b]) S.cst2[S.comp[a]]++;
+        }
+    }
+    __syncwarp();
+    // ---- level-1 clusters: closed forms for isolated pairs / boundary singletons
+    bool need_general = false;
+    for (int s = lane; s < K; s += WS) {
+        const int r = S.comp[s];
+        const int size = S.cst0[r];
+        const bool ok = (long long)S.cst2[r] == (long long)size * (size - 1) / 2 &&
+                        ((S.cst1[r] & 1) || size % 2 == 0);
+        if (!ok) continue;
+        if (size == 1) {
+            const int bd = (int)(S.sbnd[s] >> 32);
+            S.alive[s] = 1; S.y[s] = bd; S.srad[s] = bd; S.label[s] = 0; S.bpar[s] = -1;
+            S.mate[s] = MATE_BOUNDARY; S.ms[s] = s; S.mo[s] = -1; S.stop[s] = s; S.nroot[s] = -1;
+        } else if (size == 2) {
+            // partner: the other member
+            int other = -1;
+            for (int t2 = 0; t2 < K; t2++)
+                if (t2 != s && S.comp[t2] == r) { other = t2; break; }
+            const int d = pair_get(S, C, s, other);
+            const long long ba = (long long)(S.sbnd[s] >> 32), bo = (long long)(S.sbnd[other] >> 32);
+            if (d / 2 <= ba && d / 2 <= bo) {
+                S.alive[s] = 1; S.y[s] = d / 2; S.srad[s] = d / 2; S.label[s] = 0; S.bpar[s] = -1;
+                S.mate[s] = other; S.ms[s] = s; S.mo[s] = other; S.stop[s] = s; S.nroot[s] = -1;
+            } else {
+                need_general = true;
+                atomicOr(&S.cst1[r], 2);   // solve with the event loop
+            }
+        } else {
+            need_general = true;
+            atomicOr(&S.cst1[r], 2);
+        }
+    }
+    __syncwarp();
+    need_general = __any_sync(FULL, need_general);
+    if (need_general) {
+        for (int r = 0; r < K; r++) {
+            if (S.comp[r] != r || !(S.cst1[r] & 2)) continue;
+            for (int s = lane; s < K; s += WS)
+                if (S.comp[s] == r) make_root(S, s);
+            __syncwarp();
+            const int st = run_matcher(S, C, lane, nhi);
+            if (st != RUN_OK) {
+                if (st == RUN_CAP) return -1;
+                return st == RUN_NOSOL ? QEC_SHOT_NO_SOLUTION
+                       : st == RUN_BUDGET ? QEC_SHOT_BUDGET_EXCEEDED : QEC_SHOT_INTERNAL;
+            }
+            for (int s = lane; s < K; s += WS)
+                if (S.comp[s] == r) S.inplay[s] = 0;
+            __syncwarp();
+        }
+    }
+    // ---- top level: every remaining event from t = 0, level-1 states frozen
+    for (int s = lane; s < K; s += WS) {
+        if (S.alive[s] || S.stop[s] != s) S.inplay[s] = 1;   // stopped level-1 configuration
+        else make_root(S, s);
+    }
+    __syncwarp();
+    {
+        const int st = run_matcher(S, C, lane, nhi);
+        if (st != RUN_OK) {
+            if (st == RUN_CAP) return -1;
+            return st == RUN_NOSOL ? QEC_SHOT_NO_SOLUTION
+                   : st == RUN_BUDGET ? QEC_SHOT_BUDGET_EXCEEDED : QEC_SHOT_INTERNAL;
+        }
+    }
+    long long wint = 0;
+    unsigned long long ob = 0;
+    trace(S, C, lane, nhi, wint, ob);
+    const int err = __ldcg(&S.ctr[C_ERR]);
+    if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
+    w_out = wint / 2;
+    o_out = ob;
+    return QEC_SHOT_OK;
+}
+
+__device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, int lane,
+                            unsigned long long deadline) {
+    int gi = A.graph_of_shot ? A.graph_of_shot[shot] : 0;
+    if (gi < 0 || gi >= A.num_graphs) gi = 0;
+    const DGraph &g = A.g[gi];
+    const long long off = A.syn_off ? A.syn_off[shot] : shot * (long long)g.words;
+    const unsigned *row = A.syn + off;
+    int status = -1;
+    long long w = 0;
+    unsigned long long o = 0;
+    for (unsigned scale = 1; scale <= 64 && status == -1; scale *= 4)
+        status = decode_attempt(A, S, g, row, lane, scale, deadline, w, o);
+    if (status < 0) {
+        status = QEC_SHOT_CAPACITY;
+        if (A.pass == 0 && A.single_shot < 0 && lane == 0) {
+            const unsigned long long idx = atomicAdd(&A.queue[1], 1ull);
+            A.overflow[idx] = (int)shot;
+        }
+        w = 0;
+        o = 0;
+    }
+    if (lane == 0) {
+        A.w_out[shot] = w;
+        A.obs_out[shot] = o;
+        A.st_out[shot] = status;
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ BatchArgs a) {
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    Slab S;
+    carve(a.slabs + wid * a.slab_bytes, a.caps, S);
+    unsigned long long deadline = 0;
+    if (a.watchdog_ns > 0) {
+        unsigned long long t0 = lane == 0 ? now_ns() : 0;
+        deadline = __shfl_sync(FULL, t0, 0) + (unsigned long long)a.watchdog_ns;
+    }
+    if (a.single_shot >= 0) {
+        if (wid == 0) decode_shot(a, S, a.single_shot, lane, deadline);
+        return;
+    }
+    unsigned long long *counter = a.queue + (a.pass == 0 ? 0 : 2);
+    const long long limit = a.pass == 0 ? a.num_shots : (long long)min(a.queue[1], (unsigned long long)a.num_shots);
+    for (long long it = 0; it < a.num_shots + 1; it++) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if ((long long)item >= limit) break;
+        const long long shot = a.pass == 0 ? (long long)item : (long long)a.overflow[item];
+        decode_shot(a, S, shot, lane, deadline);
+    }
+}
+
+}  // namespace
+
+long long slab_bytes_for(const SlabCaps &c) {
+    Slab S;
+    long long b = carve(reinterpret_cast<char *>(0), c, S);
+    return (b + 255) & ~255LL;
+}
+
+SlabCaps caps_for_kcap(int kcap) {
+    auto p2 = [](long long x) { long long r = 1; while (r < x) r <<= 1; return (int)r; };
+    SlabCaps c;
+    c.kc = kcap;
+    c.hc = p2(64LL * kcap < 1024 ? 1024 : 64LL * kcap);
+    c.ec = 48 * kcap + 64;
+    c.wc = 48 * kcap + 64;
+    c.phc = p2(16LL * kcap < 256 ? 256 : 16LL * kcap);
+    c.nc = 2 * kcap + 16;
+    c.cc = 24 * kcap + 64;
+    return c;
+}
+
+cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s) {
+    batch_kernel<<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s) {
+    return cudaMemsetAsync(queue, 0, 4 * sizeof(unsigned long long), s);
+}
+
+}  // namespace qec

@@ -1,0 +1,73 @@
+// Internal declarations shared by the host library (capi.cpp) and the CUDA
+// kernels (decoder.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qec.h"
+
+namespace qec {
+
+// One CSR slot of a detector: neighbour detector (-1 = boundary), internal
+// weight (2w), merged edge id.  16-byte aligned so one vector load fetches it.
+struct __align__(16) Slot {
+    int nbr;
+    int w;
+    int eid;
+    int pad;
+};
+
+// Device view of one graph, passed to kernels by value.
+struct DGraph {
+    int n;             // detectors
+    int words;         // padded uint32 words per syndrome row
+    int wmax;          // largest internal weight
+    int d1, b1;        // Algorithm 3 level-1 diameter / buffer (internal units)
+    int internal_obs;  // some detector-detector edge carries an observable
+    int pad0, pad1;
+    const int *row;                   // [n + 1]
+    const Slot *slot;                 // [row[n]]
+    const unsigned long long *eobs;   // [merged edges]
+    const int2 *eend;                 // [merged edges]: (lower detector endpoint, internal weight)
+};
+
+// Capacities of one warp's slab (per-shot working set).
+struct SlabCaps {
+    int kc;    // detection events
+    int hc;    // explored-entry hash slots (power of two)
+    int ec;    // explored-entry list
+    int wc;    // relaxation work list
+    int phc;   // pair hash slots (power of two)
+    int nc;    // matcher nodes
+    int cc;    // blossom cycle pool
+};
+
+struct BatchArgs {
+    DGraph g[QEC_MAX_GRAPHS_PER_BATCH];
+    int num_graphs;
+    int band_factor;
+    long long num_shots;
+    long long max_events;
+    const int *graph_of_shot;
+    const long long *syn_off;
+    const unsigned *syn;
+    unsigned long long *obs_out;
+    long long *w_out;
+    int *st_out;
+    char *slabs;
+    long long slab_bytes;
+    SlabCaps caps;
+    unsigned long long *queue;   // [0] next work item, [1] overflow count
+    int *overflow;               // shot ids that overflowed the main pass
+    int pass;                    // 0: all shots, 1: shots listed in overflow
+    long long single_shot;       // >= 0: decode only this shot (plain path)
+    long long watchdog_ns;       // > 0: shots still running this long after the launch stop (budget status)
+};
+
+long long slab_bytes_for(const SlabCaps &c);
+SlabCaps caps_for_kcap(int kcap);
+cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s);
+
+}  // namespace qec

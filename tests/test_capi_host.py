@@ -1,0 +1,86 @@
+"""C-ABI library: builds for sm_103a, loads, exports every declared symbol, and
+its host-only logic (Algorithm 3, input validation) works without a GPU."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2609_12262_gb300 as q
+from paper_2609_12262_gb300 import build as qbuild
+from oracle import alg3
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    qbuild.build()
+    return q.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "qec.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qec_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert len(syms) >= 12
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+@pytest.mark.parametrize("wmax", [164, 170, 186, 198, 222, 9, 2])
+def test_schedule_matches_oracle(L, wmax):
+    d, b = q.schedule(wmax, levels=8)
+    od, ob, _ = alg3(wmax, levels=len(d))
+    assert len(d) >= 2
+    assert d == od and b == ob
+
+
+def test_schedule_custom_params(L):
+    d, b = q.schedule(186, q=(1, 5), phi_min=(1, 20), levels=3)
+    from fractions import Fraction
+    od, ob, _ = alg3(186, q=Fraction(1, 5), phi_min=Fraction(1, 20), levels=len(d))
+    assert d == od and b == ob
+
+
+def _desc(n, u, v, w, o, nobs=1):
+    arrs = [np.ascontiguousarray(u, np.int32), np.ascontiguousarray(v, np.int32),
+            np.ascontiguousarray(w, np.int32), np.ascontiguousarray(o, np.uint64)]
+    d = q.qec_graph_desc()
+    d.num_detectors, d.num_edges, d.num_observables = n, len(u), nobs
+    d.u = arrs[0].ctypes.data_as(C.POINTER(C.c_int32))
+    d.v = arrs[1].ctypes.data_as(C.POINTER(C.c_int32))
+    d.w = arrs[2].ctypes.data_as(C.POINTER(C.c_int32))
+    d.obs = arrs[3].ctypes.data_as(C.POINTER(C.c_uint64))
+    return d, arrs
+
+
+@pytest.mark.parametrize("case,code", [
+    (dict(n=3, u=[0, 5], v=[1, -1], w=[2, 2], o=[0, 0]), q.QEC_EINVAL),     # endpoint out of range
+    (dict(n=3, u=[0, 1], v=[0, -1], w=[2, 2], o=[0, 0]), q.QEC_EINVAL),     # self loop
+    (dict(n=3, u=[0, 1], v=[1, -1], w=[0, 2], o=[0, 0]), q.QEC_EINVAL),     # weight 0
+    (dict(n=3, u=[0, 1], v=[1, -1], w=[-3, 2], o=[0, 0]), q.QEC_EINVAL),    # negative weight
+    (dict(n=3, u=[0, 1], v=[1, -1], w=[2, 2], o=[0, 2]), q.QEC_EINVAL),     # obs bit 1 with 1 observable
+    (dict(n=0, u=[], v=[], w=[], o=[]), q.QEC_ERANGE),                      # no detectors
+])
+def test_graph_create_rejects(L, case, code):
+    d, _keep = _desc(case["n"], case["u"], case["v"], case["w"], case["o"])
+    h = C.c_void_p()
+    rc = L.qec_graph_create(C.byref(d), C.byref(h))
+    assert rc == code and not h.value
+    assert len(q.last_error()) > 0
+
+
+def test_decode_rejects_bad_args(L):
+    vp = C.c_void_p
+    arr = (vp * 1)(None)
+    assert L.qec_decode_batch(arr, 0, None, None, None, 5, None, None, None, None) == q.QEC_EINVAL
+    assert L.qec_decode_batch(arr, 1, None, None, None, -1, None, None, None, None) == q.QEC_EINVAL
+    assert L.qec_decode_batch(arr, 1, None, None, None, 0, None, None, None, None) == q.QEC_OK
+    assert L.qec_decode_batch(arr, 33, None, None, None, 5, None, None, None, None) == q.QEC_EINVAL
