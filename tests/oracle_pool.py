@@ -23,7 +23,30 @@ def _work(args):
     return _G[gi].decode_bitmaps(rows, mode)
 
 
-def oracle_decode(phys_list, graph_of_shot, rows_by_shot, mode="hier", workers=None, chunk=256):
+class OraclePool:
+    """A spawn-started pool of oracle workers holding the graphs, reused across calls."""
+
+    def __init__(self, phys_list, workers=None):
+        self.phys_list = phys_list
+        self.n = max(1, workers or (os.cpu_count() or 2))
+        ctx = mp.get_context("spawn")
+        self.ex = ProcessPoolExecutor(max_workers=self.n, mp_context=ctx, initializer=_init,
+                                      initargs=(phys_list,))
+        list(self.ex.map(_noop, range(self.n)))   # start every worker
+
+    def decode(self, graph_of_shot, rows_by_shot, mode="hier", chunk=None):
+        return oracle_decode(self.phys_list, graph_of_shot, rows_by_shot, mode=mode,
+                             chunk=chunk or max(1, len(rows_by_shot) // (4 * self.n)), executor=self.ex)
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def _noop(_):
+    return 0
+
+
+def oracle_decode(phys_list, graph_of_shot, rows_by_shot, mode="hier", workers=None, chunk=256, executor=None):
     """rows_by_shot: list/array of uint32 rows (shot s uses graph phys_list[graph_of_shot[s]]).
 
     Returns (weight int64, obs uint64, status int32) per shot.
@@ -44,7 +67,9 @@ def oracle_decode(phys_list, graph_of_shot, rows_by_shot, mode="hier", workers=N
     if not tasks:
         return W, O, st
     n = workers or max(1, min(len(tasks), (os.cpu_count() or 2)))
-    if n == 1:
+    if executor is not None:
+        results = list(executor.map(_work, tasks))
+    elif n == 1:
         _init(phys_list)
         results = [_work(t) for t in tasks]
     else:
