@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small workload (profiling)")
+    ap.add_argument("--kcap", type=int, default=0, help="detection events per main-pass slab (0 = auto)")
     return ap.parse_args()
 
 
@@ -224,6 +225,8 @@ def main():
     from paper_2609_12262_gb300 import build as qbuild
     qbuild.build()
     import paper_2609_12262_gb300 as q
+    if args.kcap:
+        q.set_tuning(kcap=args.kcap)
 
     graphs, gid, offs, syn = workload(args, rank)
     S = int(gid.shape[0])

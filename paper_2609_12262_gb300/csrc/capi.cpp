@@ -514,7 +514,7 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     const int sms = sm_count(dev);
     const int kcap = kcap_for(nmax, tune);
     SlabCaps caps = qec::caps_for_kcap(kcap);
-    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, std::min(nmax, 16 * kcap)));
+    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, std::min(nmax, 16 * kcap)), 4);
     const int wpb = std::max(1, tune.warps_per_block);
     int bps = tune.blocks_per_sm;
     if (bps <= 0) bps = std::max(1, 16 / wpb);

@@ -1026,14 +1026,15 @@ long long slab_bytes_for(const SlabCaps &c) {
     return (b + 255) & ~255LL;
 }
 
-SlabCaps caps_for_kcap(int kcap) {
+SlabCaps caps_for_kcap(int kcap, int table_factor) {
     auto p2 = [](long long x) { long long r = 1; while (r < x) r <<= 1; return (int)r; };
+    const long long f = table_factor < 1 ? 1 : table_factor;
     SlabCaps c;
     c.kc = kcap;
-    c.hc = p2(64LL * kcap < 1024 ? 1024 : 64LL * kcap);
-    c.ec = 48 * kcap + 64;
-    c.wc = 48 * kcap + 64;
-    c.phc = p2(16LL * kcap < 256 ? 256 : 16LL * kcap);
+    c.hc = p2(64LL * f * kcap < 1024 ? 1024 : 64LL * f * kcap);
+    c.ec = (int)(48 * f * kcap + 64);
+    c.wc = (int)(48 * f * kcap + 64);
+    c.phc = p2(16LL * f * kcap < 256 ? 256 : 16LL * f * kcap);
     c.nc = 2 * kcap + 16;
     c.cc = 24 * kcap + 64;
     return c;

@@ -66,7 +66,9 @@ struct BatchArgs {
 };
 
 long long slab_bytes_for(const SlabCaps &c);
-SlabCaps caps_for_kcap(int kcap);
+// Slab capacities for `kcap` detection events; hash tables and entry lists get
+// table_factor times the default room per event.
+SlabCaps caps_for_kcap(int kcap, int table_factor = 1);
 cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s);
 
