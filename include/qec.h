@@ -170,6 +170,33 @@ typedef struct {
 int qec_set_tuning(const qec_tuning *t);
 int qec_get_tuning(qec_tuning *t);
 
+/* qec_decode_batch without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory while running -- a real-time decoding loop that must not stall on the
+ * driver's allocator or fail half-way for lack of memory, or an application
+ * that reserves all device memory at start-up.  Its scratch is one static
+ * device array of QEC_STATIC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Arguments, layouts and outputs are those of qec_decode_batch.  Limits:
+ * num_shots <= QEC_STATIC_MAX_SHOTS (else QEC_ERANGE, nothing launched); a
+ * shot with more than QEC_STATIC_MAX_EVENTS detection events ends with status
+ * QEC_SHOT_CAPACITY.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the array and zeroes its
+ * work counters on `stream`: calls whose work overlaps on the GPU race, so the
+ * caller must order them (for example by issuing them on one stream). */
+#define QEC_STATIC_SCRATCH_BYTES (48LL * 1024 * 1024)
+#define QEC_STATIC_WARPS 152
+#define QEC_STATIC_MAX_EVENTS 128
+#define QEC_STATIC_MAX_SHOTS (1 << 20)
+int qec_decode_batch_static(const qec_graph *const *graphs, int32_t num_graphs,
+                            const int32_t *graph_of_shot, const int64_t *syn_offset_words,
+                            const uint32_t *syndromes, int64_t num_shots,
+                            uint64_t *obs_out, int64_t *weight_out, int32_t *status_out,
+                            qec_cuda_stream stream);
+
 /* Release the library-owned device workspace of the current device. */
 int qec_release_workspace(void);
 

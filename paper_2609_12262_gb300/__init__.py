@@ -72,6 +72,7 @@ def lib():
     L.qec_graph_merged_edges.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_uint64)]
     L.qec_decode_batch.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.qec_decode_plain.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
+    L.qec_decode_batch_static.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.qec_set_tuning.argtypes = [P(qec_tuning)]
     L.qec_get_tuning.argtypes = [P(qec_tuning)]
     _lib = L
@@ -209,6 +210,30 @@ def decode_batch(graphs, syndromes, graph_of_shot=None, syn_offset_words=None, n
     _check(lib().qec_decode_batch(arr, len(graphs), _dptr(graph_of_shot), _dptr(syn_offset_words),
                                   _dptr(syndromes), int(num_shots), _dptr(obs), _dptr(w), _dptr(st),
                                   _stream_handle(stream)))
+    return obs, w, st
+
+
+def decode_batch_static(graphs, syndromes, graph_of_shot=None, syn_offset_words=None, num_shots=None,
+                        out=None, stream=None):
+    """qec_decode_batch_static: decode_batch with scratch in the library's static
+    device array (no device allocation inside the call; see include/qec.h for
+    its limits).  `out` must be given by callers that cannot allocate."""
+    import torch
+    if isinstance(graphs, Graph):
+        graphs = [graphs]
+    if num_shots is None:
+        num_shots = int(graph_of_shot.shape[0]) if graph_of_shot is not None else \
+            int(syndromes.numel() // graphs[0].words)
+    if out is None:
+        dev = syndromes.device
+        out = (torch.empty(num_shots, dtype=torch.int64, device=dev),
+               torch.empty(num_shots, dtype=torch.int64, device=dev),
+               torch.empty(num_shots, dtype=torch.int32, device=dev))
+    obs, w, st = out
+    arr = (C.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    _check(lib().qec_decode_batch_static(arr, len(graphs), _dptr(graph_of_shot), _dptr(syn_offset_words),
+                                         _dptr(syndromes), int(num_shots), _dptr(obs), _dptr(w), _dptr(st),
+                                         _stream_handle(stream)))
     return obs, w, st
 
 

@@ -287,6 +287,18 @@ int sm_count(int dev) {
 
 }  // namespace
 
+int qec::graph_device_view(const qec_graph *g, DGraph *out, int *device) {
+    if (!g || !out || !device) return QEC_EINVAL;
+    *out = g->dg;
+    *device = g->device;
+    return QEC_OK;
+}
+
+int qec::set_last_error(int code, const char *msg) {
+    g_err = msg ? msg : "";
+    return code;
+}
+
 extern "C" {
 
 const char *qec_last_error(void) { return g_err.c_str(); }
