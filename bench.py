@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small workload (profiling)")
     ap.add_argument("--kcap", type=int, default=0, help="detection events per main-pass slab (0 = auto)")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     return ap.parse_args()
 
 
@@ -239,6 +240,13 @@ def main():
            torch.empty(S, dtype=torch.int32, device=dev))
     stream = torch.cuda.current_stream()
 
+    tuned = None
+    if not args.no_autotune and not args.kcap:
+        from paper_2609_12262_gb300 import autotune
+        n_tune = min(S, 160000)
+        tuned, _ = autotune.tune(qgraphs, t_syn, t_gid[:n_tune], t_off[:n_tune], budget_s=40.0)
+        autotune.apply(tuned)
+
     def step():
         q.decode_batch(qgraphs, t_syn, t_gid, t_off, num_shots=S, out=out, stream=stream)
 
@@ -353,11 +361,14 @@ def main():
             "config": {"workload": "batched decode, %d shots: d in {7,...,21} x %d shots, d rounds, p=%g, "
                        "one persistent launch" % (S, args.shots_per_d, args.p),
                        "shots": S, "p": args.p, "distances": DS, "parallelism": "replicas" if ws > 1 else "1 GPU",
-                       "l2": "inputs (%.0f MB of syndromes) larger than L2; no flush" % (4 * words.sum() / 1e6)},
+                       "l2": ("inputs (%.0f MB of syndromes) larger than the 129 MB L2; no flush" % (4 * words.sum() / 1e6))
+                       if 4 * words.sum() > 129e6 else "inputs smaller than L2 (profiling size)"},
             "us_per_round": 1e6 / value * ws / mean_d,
             "plain_gpu": {"value": plain, "unit": UNIT, "shots": args.plain_shots,
                           "speedup_batched": (value / ws / plain) if plain else None},
             "nonzero_status_shots": bad_status,
+            "tuning": q.get_tuning(),
+            "autotuned": {k: tuned[k] for k in ("candidates", "ms", "shots")} if tuned else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_source": peak_kind,

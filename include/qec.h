@@ -159,7 +159,11 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
                      qec_cuda_stream stream);
 
 /* Tuning knobs of the batched path (chosen by the autotuner in the Python
- * binding; all have safe defaults).  Zero keeps the current value. */
+ * binding; all have safe defaults).  In qec_set_tuning a positive value sets
+ * a knob, zero keeps its current value and a negative value restores the
+ * default (warps_per_block 4, blocks_per_sm 0 = as many as fit, band_factor 1,
+ * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, max_events 4e6).
+ * qec_get_tuning reports 0 for the automatic choices. */
 typedef struct {
     int32_t warps_per_block;   /* 1 .. 32 */
     int32_t blocks_per_sm;     /* 1 .. 64 */
@@ -187,7 +191,7 @@ int qec_get_tuning(qec_tuning *t);
  * call before any stream capture.  Every call shares the array and zeroes its
  * work counters on `stream`: calls whose work overlaps on the GPU race, so the
  * caller must order them (for example by issuing them on one stream). */
-#define QEC_STATIC_SCRATCH_BYTES (48LL * 1024 * 1024)
+#define QEC_STATIC_SCRATCH_BYTES (64LL * 1024 * 1024)
 #define QEC_STATIC_WARPS 152
 #define QEC_STATIC_MAX_EVENTS 128
 #define QEC_STATIC_MAX_SHOTS (1 << 20)

@@ -467,15 +467,16 @@ int qec_graph_merged_edges(const qec_graph *g, int32_t *u, int32_t *v, int32_t *
 
 int qec_set_tuning(const qec_tuning *t) {
     if (!t) return fail(QEC_EINVAL, "NULL tuning");
-    if (t->warps_per_block < 0 || t->warps_per_block > 32 || t->blocks_per_sm < 0 || t->blocks_per_sm > 64 ||
-        t->band_factor < 0 || t->band_factor > 64 || t->kcap < 0 || t->max_events < 0)
+    if (t->warps_per_block > 32 || t->blocks_per_sm > 64 || t->band_factor > 64 || t->kcap > (1 << 18))
         return fail(QEC_EINVAL, "tuning value out of range");
+    static const qec_tuning defaults = {4, 0, 1, 0, 4000000};
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (t->warps_per_block) g_tune.warps_per_block = t->warps_per_block;
-    if (t->blocks_per_sm) g_tune.blocks_per_sm = t->blocks_per_sm;
-    if (t->band_factor) g_tune.band_factor = t->band_factor;
-    if (t->kcap) g_tune.kcap = t->kcap;
-    if (t->max_events) g_tune.max_events = t->max_events;
+    auto pick = [](auto v, auto cur, auto def) { return v > 0 ? v : (v < 0 ? def : cur); };
+    g_tune.warps_per_block = pick(t->warps_per_block, g_tune.warps_per_block, defaults.warps_per_block);
+    g_tune.blocks_per_sm = pick(t->blocks_per_sm, g_tune.blocks_per_sm, defaults.blocks_per_sm);
+    g_tune.band_factor = pick(t->band_factor, g_tune.band_factor, defaults.band_factor);
+    g_tune.kcap = pick(t->kcap, g_tune.kcap, defaults.kcap);
+    g_tune.max_events = pick(t->max_events, g_tune.max_events, defaults.max_events);
     return QEC_OK;
 }
 
@@ -526,10 +527,10 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     const int sms = sm_count(dev);
     const int kcap = kcap_for(nmax, tune);
     SlabCaps caps = qec::caps_for_kcap(kcap);
-    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, std::min(nmax, 16 * kcap)), 4);
-    const int wpb = std::max(1, tune.warps_per_block);
+    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, std::min(nmax, 4 * kcap)), 2);
+    const int wpb = std::max(1, std::min(tune.warps_per_block, qec::max_block_threads() / 32));
     int bps = tune.blocks_per_sm;
-    if (bps <= 0) bps = std::max(1, 16 / wpb);
+    if (bps <= 0) bps = qec::occupancy_blocks(32 * wpb);
     long long nwarps = plain ? 1 : (long long)sms * bps * wpb;
     long long nwarps2 = plain ? 1 : (long long)sms;
     if (plain) caps = caps2;

@@ -41,6 +41,9 @@
 #include "qec_internal.h"
 
 #define WS 32   // lanes per warp
+#ifndef QEC_MIN_BLOCKS
+#define QEC_MIN_BLOCKS 6   // 128-thread blocks per SM the register budget must allow
+#endif
 
 namespace qec {
 
@@ -59,7 +62,7 @@ enum { MATE_NONE = -1, MATE_BOUNDARY = -2 };
 
 // slab counters
 enum { C_ECOUNT = 0, C_WL = 1, C_NPAIRS = 2, C_CCOUNT = 3, C_NFREE = 4, C_ERR = 5, C_HFILL = 6, C_NHI = 7,
-       C_TOTAL = 16 };
+       C_TL = 8, C_CHANGED = 9, C_TOTAL = 16 };
 enum { ERR_CAP = 1, ERR_INTERNAL = 2 };
 
 __device__ __forceinline__ unsigned long long ev_key(long long t, int kind, int lo, int hi) {
@@ -90,7 +93,9 @@ struct Slab {
     // explored entries: key (vertex << 32 | source), value exact distance
     unsigned long long *hkey;
     int *hval;
-    int *ent, *wl0, *wl1;
+    int *ent;
+    unsigned long long *wl0, *wl1, *tl;   // (vertex << 32 | source) work lists / new entries
+    int *xsrc, *xR, *xcnt, *xcur;         // sources being extended, target radii, band counts
     // pairs: key (lo << 32 | hi), value distance, list of used slots
     unsigned long long *pkey;
     int *pval, *plist;
@@ -117,7 +122,10 @@ __host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &
     S.cst0 = bump<int>(p, c.kc); S.cst1 = bump<int>(p, c.kc); S.cst2 = bump<int>(p, c.kc);
     S.sbnd = bump<unsigned long long>(p, c.kc);
     S.hkey = bump<unsigned long long>(p, c.hc); S.hval = bump<int>(p, c.hc);
-    S.ent = bump<int>(p, c.ec); S.wl0 = bump<int>(p, c.wc); S.wl1 = bump<int>(p, c.wc);
+    S.ent = bump<int>(p, c.ec);
+    S.wl0 = bump<unsigned long long>(p, c.wc); S.wl1 = bump<unsigned long long>(p, c.wc);
+    S.tl = bump<unsigned long long>(p, c.ec);
+    S.xsrc = bump<int>(p, c.kc); S.xR = bump<int>(p, c.kc); S.xcnt = bump<int>(p, c.kc); S.xcur = bump<int>(p, c.kc);
     S.pkey = bump<unsigned long long>(p, c.phc); S.pval = bump<int>(p, c.phc); S.plist = bump<int>(p, c.phc);
     S.y = bump<int>(p, c.nc); S.bpar = bump<int>(p, c.nc); S.label = bump<int>(p, c.nc);
     S.tpar = bump<int>(p, c.nc); S.tps = bump<int>(p, c.nc); S.tpo = bump<int>(p, c.nc);
@@ -265,22 +273,46 @@ __device__ __forceinline__ void bnd_update(const Slab &S, int s, int d, int eid)
     atomicMin(&S.sbnd[s], v);
 }
 
-// Grow the explored ball of source s from radius sR[s] to Rn (Rn - sR[s] >= wmax).
-// All lanes call; warp-uniform.
-__device__ void extend(const Slab &S, const Shot &C, int s, int Rn, int lane) {
+__device__ __forceinline__ unsigned long long vs_pack(int v, int s) {
+    return ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
+}
+
+// Grow the explored balls of the sources xsrc[0 .. nx) from radius sR[s] to
+// xR[i] (xR[i] - sR[s] >= largest weight), all at once: the previous band of
+// each source is the frontier, label-correcting relaxation runs on (vertex,
+// source) work lists until no distance changes, every new entry is checked
+// for contacts with the other sources' balls, and each source's new band is
+// stored contiguously in `ent` as its next frontier.  All lanes call.
+__device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
     const DGraph &g = C.g;
-    const int fb = S.sbeg[s], fc = S.scnt[s];
-    const int band_beg = __ldcg(&S.ctr[C_ECOUNT]);
-    const int *F = S.ent + fb;
-    int nf = fc;
-    int *Wn = S.wl0, *Wo = S.wl1;
+    if (nx <= 0) return;
+    __syncwarp();
+    if (lane == 0) { S.ctr[C_TL] = 0; S.ctr[C_WL] = 0; }
+    for (int i = lane; i < nx; i += WS) S.xcnt[i] = 0;
+    __syncwarp();
+    // initial frontier: the previous band of every listed source
+    for (int i = lane; i < nx; i += WS) {
+        const int s = S.xsrc[i];
+        const int fb = S.sbeg[s], fc = S.scnt[s];
+        const int base = atomicAdd(&S.ctr[C_WL], fc);
+        for (int k = 0; k < fc; k++) {
+            if (base + k < C.wc) S.wl0[base + k] = vs_pack(S.ent[fb + k], i);
+            else set_err(S, ERR_CAP);
+        }
+    }
+    __syncwarp();
+    int nf = min(__ldcg(&S.ctr[C_WL]), C.wc);
+    unsigned long long *F = S.wl0, *Wn = S.wl1;
     for (int iter = 0;; iter++) {
         if (iter >= 4096) { if (lane == 0) set_err(S, ERR_INTERNAL); break; }
         __syncwarp();
         if (lane == 0) S.ctr[C_WL] = 0;
         __syncwarp();
         for (int i = lane; i < nf; i += WS) {
-            const int x = F[i];
+            const unsigned long long it = F[i];
+            const int x = (int)(it >> 32), xi = (int)(unsigned)(it & 0xffffffffu);
+            const int s = S.xsrc[xi];
+            const int Rn = S.xR[xi];
             const int dx = ht_get(S, C, x, s);
             const int r0 = __ldg(g.row + x), r1 = __ldg(g.row + x + 1);
             for (int j = r0; j < r1; j++) {
@@ -290,33 +322,55 @@ __device__ void extend(const Slab &S, const Shot &C, int s, int Rn, int lane) {
                 if (nd > Rn) continue;
                 int r = ht_upsert(S, C, sl.nbr, s, nd);
                 if (r == 1) {
-                    int e = atomicAdd(&S.ctr[C_ECOUNT], 1);
-                    if (e < C.ec) S.ent[e] = sl.nbr; else set_err(S, ERR_CAP);
+                    const int e = atomicAdd(&S.ctr[C_TL], 1);
+                    if (e < C.ec) S.tl[e] = vs_pack(sl.nbr, xi); else set_err(S, ERR_CAP);
                 }
                 if (r >= 1) {
-                    int w = atomicAdd(&S.ctr[C_WL], 1);
-                    if (w < C.wc) Wn[w] = sl.nbr; else set_err(S, ERR_CAP);
+                    const int w = atomicAdd(&S.ctr[C_WL], 1);
+                    if (w < C.wc) Wn[w] = vs_pack(sl.nbr, xi); else set_err(S, ERR_CAP);
                 }
             }
         }
         __syncwarp();
-        int nw = __ldcg(&S.ctr[C_WL]);
-        int err = __ldcg(&S.ctr[C_ERR]);
+        const int nw = __ldcg(&S.ctr[C_WL]);
+        const int err = __ldcg(&S.ctr[C_ERR]);
         if (nw == 0 || err) break;
-        F = Wn;
-        nf = nw;
-        int *t = Wn; Wn = Wo; Wo = t;
+        nf = min(nw, C.wc);
+        unsigned long long *t = F; F = Wn; Wn = t;
     }
     __syncwarp();
-    const int band_end = min(__ldcg(&S.ctr[C_ECOUNT]), C.ec);
+    const int nt = min(__ldcg(&S.ctr[C_TL]), C.ec);
+    const int e0 = __ldcg(&S.ctr[C_ECOUNT]);
+    if (e0 + nt > C.ec) { if (lane == 0) set_err(S, ERR_CAP); __syncwarp(); return; }
+    // bands made contiguous per source (counting sort of the new entries)
+    for (int i = lane; i < nt; i += WS) atomicAdd(&S.xcnt[(int)(unsigned)(S.tl[i] & 0xffffffffu)], 1);
+    __syncwarp();
     if (lane == 0) {
-        S.sR[s] = Rn;
-        S.sbeg[s] = band_beg;
-        S.scnt[s] = band_end - band_beg;
-        if (band_end == band_beg) S.sexh[s] = 1;
+        int acc = e0;
+        for (int i = 0; i < nx; i++) {
+            const int s = S.xsrc[i];
+            const int c = S.xcnt[i];
+            S.xcur[i] = acc;
+            S.sbeg[s] = acc;
+            S.scnt[s] = c;
+            S.sR[s] = S.xR[i];
+            if (c == 0) S.sexh[s] = 1;
+            acc += c;
+        }
+        S.ctr[C_ECOUNT] = acc;
     }
-    for (int i = band_beg + lane; i < band_end; i += WS) {
-        const int yv = S.ent[i];
+    __syncwarp();
+    for (int i = lane; i < nt; i += WS) {
+        const unsigned long long it = S.tl[i];
+        const int pos = atomicAdd(&S.xcur[(int)(unsigned)(it & 0xffffffffu)], 1);
+        S.ent[pos] = (int)(it >> 32);
+    }
+    __syncwarp();
+    // contacts of every new entry with the other sources' balls
+    for (int i = lane; i < nt; i += WS) {
+        const unsigned long long it = S.tl[i];
+        const int yv = (int)(it >> 32);
+        const int s = S.xsrc[(int)(unsigned)(it & 0xffffffffu)];
         const int dy = ht_get(S, C, yv, s);
         contacts_at(S, C, s, yv, dy);
         const int r0 = __ldg(g.row + yv), r1 = __ldg(g.row + yv + 1);
@@ -326,6 +380,13 @@ __device__ void extend(const Slab &S, const Shot &C, int s, int Rn, int lane) {
         }
     }
     __syncwarp();
+}
+
+// Grow one source's ball by one band.  All lanes call.
+__device__ void extend_one(const Slab &S, const Shot &C, int s, int lane) {
+    if (lane == 0) { S.xsrc[0] = s; S.xR[0] = S.sR[s] + C.band; }
+    __syncwarp();
+    extend_many(S, C, 1, lane);
 }
 
 // ---------------------------------------------------------------- matcher --
@@ -604,8 +665,18 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
         C.t = tn;
         __syncwarp();
         if (kind == EV_EXTEND) {
-            const int s = lo;
-            extend(S, C, s, S.sR[s] + C.band, lane);
+            // every growing region that reached its explored radius now
+            if (lane == 0) S.ctr[C_WL] = 0;
+            __syncwarp();
+            for (int s = lane; s < C.K; s += WS) {
+                if (S.inplay[s] && !S.sexh[s] && S.label[S.stop[s]] == 1 && S.srad[s] == S.sR[s] + 1) {
+                    const int k = atomicAdd(&S.ctr[C_WL], 1);
+                    S.xsrc[k] = s;
+                    S.xR[k] = S.sR[s] + C.band;
+                }
+            }
+            __syncwarp();
+            extend_many(S, C, __ldcg(&S.ctr[C_WL]), lane);
         } else if (kind == EV_IMPLODE) {
             ev_shatter(S, C, S.stop[lo], lane);
         } else if (kind == EV_BOUNDARY) {
@@ -636,7 +707,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
 // distance dx: predecessor = lowest edge id among tight edges.  All lanes call.
 __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int dx, int lane) {
     const DGraph &g = C.g;
-    for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s]; n++) extend(S, C, s, S.sR[s] + C.band, lane);
+    for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s] && !__ldcg(&S.ctr[C_ERR]); n++) extend_one(S, C, s, lane);
     unsigned long long o = 0;
     const int src = S.svtx[s];
     int cur = x, dcur = dx;
@@ -803,7 +874,7 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
                               unsigned long long &o_out) {
     Shot C;
     C.g = g;
-    C.ec = A.caps.ec; C.wc = A.caps.wc; C.nc = A.caps.nc; C.cc = A.caps.cc;
+    C.ec = A.caps.ec; C.wc = A.caps.wc; C.cc = A.caps.cc;
     C.band = max(g.wmax, 1) * max(A.band_factor, 1);
     C.events = 0;
     C.t = 0;
@@ -813,9 +884,12 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     C.K = K;
     C.max_events = min(A.max_events, 256LL * K + 4096);
     if (K == 0) { w_out = 0; o_out = 0; return QEC_SHOT_OK; }
-    if (K > ID_MAX - 1 || 2 * K + 8 > C.nc) return -2;
-    const unsigned hs = min(next_pow2(max(256u, 64u * (unsigned)K * scale)), (unsigned)A.caps.hc);
-    const unsigned ps = min(next_pow2(max(64u, 16u * (unsigned)K * scale)), (unsigned)A.caps.phc);
+    if (K > ID_MAX - 1 || 2 * K + 8 > A.caps.nc) return -2;
+    C.nc = min(A.caps.nc, 2 * K + 16);   // leaves + at most K blossoms alive at once
+    // about 7 explored entries and 1 pair per detection event at the design
+    // point; the tables stay at most half full or the shot is retried larger
+    const unsigned hs = min(next_pow2(max(128u, 32u * (unsigned)K * scale)), (unsigned)A.caps.hc);
+    const unsigned ps = min(next_pow2(max(64u, 8u * (unsigned)K * scale)), (unsigned)A.caps.phc);
     C.hmask = hs - 1;
     C.pmask = ps - 1;
     clear_tables(S, C, lane);
@@ -852,41 +926,48 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     __syncwarp();
     // ---- Algorithm 1, level 1: balls of radius max(b1/2, band) around every event
     const int R1 = max(g.b1 / 2, C.band);
-    for (int s = 0; s < K; s++) {
-        extend(S, C, s, R1, lane);
-        if (__ldcg(&S.ctr[C_ERR])) break;
-    }
+    for (int s = lane; s < K; s += WS) { S.xsrc[s] = s; S.xR[s] = R1; }
+    __syncwarp();
+    extend_many(S, C, K, lane);
     {
         const int err = __ldcg(&S.ctr[C_ERR]);
         if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
     }
     const int npairs = __ldcg(&S.ctr[C_NPAIRS]);
-    if (lane == 0) {
-        for (int s = 0; s < K; s++) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
-        for (int i = 0; i < npairs; i++) {
+    // connected components of pairs within b_1: min-label propagation
+    for (int s = lane; s < K; s += WS) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
+    __syncwarp();
+    for (int round = 0; round <= K; round++) {
+        bool changed = false;
+        for (int i = lane; i < npairs; i += WS) {
             const int sl = S.plist[i];
-            if (S.pval[sl] > g.b1) continue;
-            const unsigned long long k = S.pkey[sl];
-            int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
-            while (S.comp[a] != a) a = S.comp[a];
-            while (S.comp[b] != b) b = S.comp[b];
-            if (a != b) { if (a < b) S.comp[b] = a; else S.comp[a] = b; }
-        }
-        for (int s = 0; s < K; s++) {
-            int r = s;
-            while (S.comp[r] != r) r = S.comp[r];
-            S.comp[s] = r;
-            S.cst0[r]++;
-            const unsigned long long bb = S.sbnd[s];
-            if (bb != EMPTY64 && 2LL * (long long)(bb >> 32) <= (long long)g.b1) S.cst1[r] = 1;
-        }
-        for (int i = 0; i < npairs; i++) {
-            const int sl = S.plist[i];
-            if (S.pval[sl] > g.d1) continue;
-            const unsigned long long k = S.pkey[sl];
+            if (__ldcg(&S.pval[sl]) > g.b1) continue;
+            const unsigned long long k = __ldcg(&S.pkey[sl]);
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
-            if (S.comp[a] == S.comp[b]) S.cst2[S.comp[a]]++;
+            const int la = __ldcg(&S.comp[a]), lb = __ldcg(&S.comp[b]);
+            if (la != lb) {
+                const int m = min(la, lb);
+                atomicMin(&S.comp[a], m);
+                atomicMin(&S.comp[b], m);
+                changed = true;
+            }
         }
+        __syncwarp();
+        if (!__any_sync(FULL, changed)) break;
+    }
+    for (int s = lane; s < K; s += WS) {
+        const int r = S.comp[s];
+        atomicAdd(&S.cst0[r], 1);
+        const unsigned long long bb = S.sbnd[s];
+        if (bb != EMPTY64 && 2LL * (long long)(bb >> 32) <= (long long)g.b1) atomicOr(&S.cst1[r], 1);
+    }
+    __syncwarp();
+    for (int i = lane; i < npairs; i += WS) {
+        const int sl = S.plist[i];
+        if (__ldcg(&S.pval[sl]) > g.d1) continue;
+        const unsigned long long k = __ldcg(&S.pkey[sl]);
+        const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
+        if (S.comp[a] == S.comp[b]) atomicAdd(&S.cst2[S.comp[a]], 1);
     }
     __syncwarp();
     // ---- level-1 clusters: closed forms for isolated pairs / boundary singletons
@@ -992,7 +1073,7 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, i
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(256, 2) batch_kernel(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(128, QEC_MIN_BLOCKS) batch_kernel(const __grid_constant__ BatchArgs a) {
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     Slab S;
@@ -1043,6 +1124,18 @@ SlabCaps caps_for_kcap(int kcap, int table_factor) {
 cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s) {
     batch_kernel<<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+int max_block_threads() {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, batch_kernel) != cudaSuccess) return 32;
+    return fa.maxThreadsPerBlock > 0 ? fa.maxThreadsPerBlock : 32;
+}
+
+int occupancy_blocks(int block_threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel, block_threads, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s) {

@@ -71,6 +71,10 @@ long long slab_bytes_for(const SlabCaps &c);
 SlabCaps caps_for_kcap(int kcap, int table_factor = 1);
 cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s);
+// Resident blocks per SM of the batch kernel at this block size.
+int occupancy_blocks(int block_threads);
+// Largest block the batch kernel accepts.
+int max_block_threads();
 // Device view and device id of a created graph (QEC_EINVAL for NULL).
 int graph_device_view(const qec_graph *g, DGraph *out, int *device);
 // Record the calling thread's error text for qec_last_error; returns code.

@@ -158,3 +158,24 @@ def test_band_width_does_not_change_results(qd, band):
         qd.set_tuning(band_factor=1)
     ref = oracle_decode([pg], np.zeros(500, np.int32), list(syn))
     assert_same(a, ref, "band %d" % band)
+
+
+def test_autotuner_candidates_agree_and_match_oracle(qd):
+    """Every launch shape / slab size the autotuner tries returns identical
+    results (it raises otherwise); the chosen one matches the oracle."""
+    import torch
+    from paper_2609_12262_gb300 import autotune
+    graphs, gid, offs, syn = mixed_batch([7, 11, 15, 21], 200, 0.003, seed=31)
+    gg = [qd.Graph.from_phys(pg) for pg in graphs]
+    t_syn = torch.from_numpy(syn.view(np.int32)).cuda()
+    t_gid = torch.from_numpy(gid.astype(np.int32)).cuda()
+    t_off = torch.from_numpy(offs.astype(np.int64)).cuda()
+    best, results = autotune.tune(gg, t_syn, t_gid, t_off, reps=1, budget_s=30.0, save=False)
+    assert len(results) >= 4
+    autotune.apply(best)
+    try:
+        gpu = gpu_decode(qd, gg, (syn, offs), gid=gid)
+    finally:
+        qd.set_tuning(warps_per_block=-1, blocks_per_sm=-1, band_factor=-1, kcap=-1)
+    rows = [syn[offs[s]:offs[s] + graphs[gid[s]].words] for s in range(gid.shape[0])]
+    assert_same(gpu, oracle_decode(graphs, gid, rows), "autotuned")
