@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="small workload (profiling)")
     ap.add_argument("--kcap", type=int, default=0, help="detection events per main-pass slab (0 = auto)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--serve-seconds", type=float, default=2.5, help="serving run length (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=200000.0, help="Poisson arrival rate, windows/s")
     return ap.parse_args()
 
 
@@ -169,6 +171,62 @@ def cpu_oracle_rate(graphs, gid, offs, syn, seconds, workers=None):
     return done / t_used, done, t_used, ncores
 
 
+def serving_run(q, args, dev):
+    """Poisson arrivals into a qec_stream; latency = result time - scheduled arrival."""
+    import torch
+    sds = [9, 13, 17, 21, 25]
+    N = int(args.serve_rate * args.serve_seconds)
+    per_d = (N + len(sds) - 1) // len(sds)
+    graphs, gid, offs, syn = mixed_batch(sds, per_d, args.p, seed=args.seed + 77)
+    gid, offs = gid[:N], offs[:N]
+    gg = [q.Graph.from_phys(g) for g in graphs]
+    rng = np.random.default_rng(args.seed + 78)
+    arr = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=N))
+    st = q.Stream(device_budget_bytes=6 << 30, max_inflight=65536)
+    try:
+        warm = min(2000, N)
+        i = 0
+        while i < warm:
+            i += st.submit_many(gg, gid[i:warm], offs[i:warm], syn, np.arange(i, warm, dtype=np.uint64) + (1 << 40))
+        st.flush()
+        st.poll()
+        t0 = time.monotonic_ns() + 2_000_000
+        sched = t0 + (arr * 1e9).astype(np.int64)
+        ids = np.arange(N, dtype=np.uint64)
+        got_w = np.zeros(N, np.int64); got_o = np.zeros(N, np.uint64); got_s = np.full(N, -1, np.int32)
+        t_done = np.zeros(N, np.int64)
+        i, n_done = 0, 0
+        deadline = time.monotonic() + 30 + 4 * args.serve_seconds
+        while n_done < N and time.monotonic() < deadline:
+            now = time.monotonic_ns()
+            j = int(np.searchsorted(sched, now, side="right"))
+            if j > i:
+                i += st.submit_many(gg, gid[i:j], offs[i:j], syn, ids[i:j])
+            r = st.poll()
+            if len(r):
+                k = r["request_id"].astype(np.int64)
+                got_w[k] = r["weight"]; got_o[k] = r["obs"]; got_s[k] = r["status"]; t_done[k] = r["t_done_ns"]
+                n_done += len(r)
+    finally:
+        st.close()
+    ok = got_s >= 0
+    lat_us = (t_done[ok] - sched[ok]) / 1e3
+    span = (t_done[ok].max() - t0) / 1e9 if ok.any() else float("nan")
+    # same windows through the batched path: every served result must agree
+    t_syn = torch.from_numpy(syn.view(np.int32)).to(dev)
+    o, w, s_ = q.decode_batch(gg, t_syn, torch.from_numpy(gid.astype(np.int32)).to(dev),
+                              torch.from_numpy(offs.astype(np.int64)).to(dev), num_shots=N)
+    torch.cuda.synchronize()
+    bw, bo, bs = w.cpu().numpy(), q.to_uint64(o), s_.cpu().numpy()
+    mism = int(np.count_nonzero(ok & ((bw != got_w) | (bo != got_o) | (bs != got_s))))
+    return {"windows": N, "completed": int(ok.sum()), "offered_rate": args.serve_rate,
+            "sustained": float(ok.sum() / span), "unit": "windows/s",
+            "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
+            "p999_us": float(np.percentile(lat_us, 99.9)), "max_us": float(lat_us.max()),
+            "distances": sds, "p": args.p, "mismatch_vs_batch": mism,
+            "latency": "result available on the host minus the scheduled Poisson arrival"}
+
+
 def reference_arm(args, ws, rank):
     if ws > 1 and rank != 0:
         return
@@ -213,6 +271,7 @@ def main():
         args.shots_per_d = min(args.shots_per_d, 2500)
         args.plain_shots = min(args.plain_shots, 200)
         args.no_cpu_baseline = True
+        args.serve_seconds = 0
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
     import torch
@@ -346,6 +405,10 @@ def main():
         e2e = {"value": ws * S / (e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        serving = serving_run(q, args, dev)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, secs, cores = cpu_oracle_rate(graphs, gid, offs, syn, args.cpu_seconds)
@@ -376,6 +439,7 @@ def main():
             "clocks": clocks,
             "gpu_launches": 2 * args.steps,
             "e2e": e2e,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -201,6 +201,65 @@ int qec_decode_batch_static(const qec_graph *const *graphs, int32_t num_graphs,
                             uint64_t *obs_out, int64_t *weight_out, int32_t *status_out,
                             qec_cuda_stream stream);
 
+/* ------------------------------------------------------------ serving --
+ * A request loop for syndrome windows that arrive one at a time (continuous
+ * batching).  qec_stream_submit copies one window into the micro-batch being
+ * filled; a dispatcher thread owned by the stream launches that micro-batch as
+ * soon as one of the stream's in-flight slots is free, so requests that arrive
+ * while others are on the GPU join the next launch and several launches
+ * overlap on the device (one CUDA stream and scratch workspace per slot).
+ * Graphs stay resident; results are read back into pinned memory and handed
+ * out by qec_stream_poll.  Each result is the same as decoding the window
+ * alone with qec_decode_batch. */
+#define QEC_STREAM_MAX_WORDS 2304          /* largest window: 73,728 detectors */
+#define QEC_STREAM_MAX_GRAPHS QEC_MAX_GRAPHS_PER_BATCH
+
+typedef struct {
+    uint64_t request_id;
+    uint64_t obs;          /* predicted observable flips */
+    int64_t weight;        /* matching weight, original units */
+    int32_t status;        /* QEC_SHOT_* */
+    int32_t graph_index;   /* index of the graph in the stream's registry */
+    int64_t t_submit_ns;   /* CLOCK_MONOTONIC time of qec_stream_submit */
+    int64_t t_done_ns;     /* CLOCK_MONOTONIC time the result became available */
+} qec_result;
+
+/* Create a serving stream on the current device.  device_budget_bytes bounds
+ * the device memory of the stream's in-flight slots (each slot: scratch for
+ * 2 warps per SM with room for 512 detection events per window, an overflow
+ * pass for larger windows, and window/result buffers); it must hold at least
+ * two slots (QEC_ENOMEM otherwise) and at most eight are used.  max_inflight
+ * (>= 1) bounds the windows admitted (queued or on the GPU) at once.
+ * Errors: QEC_EINVAL, QEC_ENOMEM, QEC_ECUDA. */
+int qec_stream_create(size_t device_budget_bytes, int32_t max_inflight, qec_stream **out);
+
+/* Submit one window: `syndrome_host` holds words_per_shot(g) uint32 words
+ * (host memory, copied before return).  Returns QEC_EAGAIN when max_inflight
+ * windows are admitted or the filling micro-batch is full (poll, then retry),
+ * QEC_ERANGE when the graph's rows exceed QEC_STREAM_MAX_WORDS or more than
+ * QEC_STREAM_MAX_GRAPHS distinct graphs are used, QEC_EINVAL for NULL
+ * arguments or a graph on another device. */
+int qec_stream_submit(qec_stream *s, const qec_graph *g, const uint32_t *syndrome_host,
+                      uint64_t request_id);
+
+/* Submit n windows in order, stopping at the first one that is not admitted
+ * (same rules as qec_stream_submit); *n_accepted = windows taken.  Window i
+ * uses graphs[graph_of_req[i]] and starts at syn_offset_words[i] in
+ * syndromes_host (host arrays). */
+int qec_stream_submit_many(qec_stream *s, const qec_graph *const *graphs, int32_t num_graphs,
+                           const int32_t *graph_of_req, const int64_t *syn_offset_words,
+                           const uint32_t *syndromes_host, const uint64_t *request_ids, int32_t n,
+                           int32_t *n_accepted);
+
+/* Move up to max finished results to out (host array); *n_out = count.  Never blocks. */
+int qec_stream_poll(qec_stream *s, qec_result *out, int32_t max, int32_t *n_out);
+
+/* Block until every admitted window has finished (results stay pollable). */
+int qec_stream_flush(qec_stream *s);
+
+/* Stop the dispatcher, wait for in-flight work, free everything. */
+int qec_stream_destroy(qec_stream *s);
+
 /* Release the library-owned device workspace of the current device. */
 int qec_release_workspace(void);
 

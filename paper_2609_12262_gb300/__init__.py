@@ -50,6 +50,11 @@ class qec_tuning(C.Structure):
                 ("kcap", C.c_int32), ("max_events", C.c_int64)]
 
 
+class qec_result(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("obs", C.c_uint64), ("weight", C.c_int64), ("status", C.c_int32),
+                ("graph_index", C.c_int32), ("t_submit_ns", C.c_int64), ("t_done_ns", C.c_int64)]
+
+
 _lib = None
 
 
@@ -73,6 +78,12 @@ def lib():
     L.qec_decode_batch.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.qec_decode_plain.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
     L.qec_decode_batch_static.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+    L.qec_stream_create.argtypes = [C.c_size_t, C.c_int32, P(vp)]
+    L.qec_stream_submit.argtypes = [vp, vp, vp, C.c_uint64]
+    L.qec_stream_poll.argtypes = [vp, P(qec_result), C.c_int32, P(C.c_int32)]
+    L.qec_stream_submit_many.argtypes = [vp, P(vp), C.c_int32, vp, vp, vp, vp, C.c_int32, P(C.c_int32)]
+    L.qec_stream_flush.argtypes = [vp]
+    L.qec_stream_destroy.argtypes = [vp]
     L.qec_set_tuning.argtypes = [P(qec_tuning)]
     L.qec_get_tuning.argtypes = [P(qec_tuning)]
     _lib = L
@@ -251,6 +262,64 @@ def decode_plain(graph, syndromes, num_shots=None, out=None, stream=None):
     _check(lib().qec_decode_plain(graph.handle, _dptr(syndromes), int(num_shots), _dptr(obs), _dptr(w),
                                   _dptr(st), _stream_handle(stream)))
     return obs, w, st
+
+
+class Stream:
+    """qec_stream_*: continuous-batching request loop on the current device."""
+
+    def __init__(self, device_budget_bytes: int = 6 << 30, max_inflight: int = 65536):
+        h = C.c_void_p()
+        _check(lib().qec_stream_create(int(device_budget_bytes), int(max_inflight), C.byref(h)))
+        self._h = h
+        self._buf = (qec_result * 65536)()
+
+    def submit(self, graph, syndrome_row: np.ndarray, request_id: int) -> bool:
+        """Copy one window in; False when admission is full (QEC_EAGAIN)."""
+        row = np.ascontiguousarray(syndrome_row, np.uint32)
+        rc = lib().qec_stream_submit(self._h, graph.handle, C.c_void_p(row.ctypes.data), int(request_id))
+        if rc == QEC_EAGAIN:
+            return False
+        _check(rc)
+        return True
+
+    def submit_many(self, graphs, graph_of_req, syn_offset_words, syndromes, request_ids) -> int:
+        """Submit windows in order until admission is full; returns how many were taken."""
+        arr = (C.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+        gi = np.ascontiguousarray(graph_of_req, np.int32)
+        of = np.ascontiguousarray(syn_offset_words, np.int64)
+        sy = np.ascontiguousarray(syndromes, np.uint32)
+        ri = np.ascontiguousarray(request_ids, np.uint64)
+        n = C.c_int32(0)
+        _check(lib().qec_stream_submit_many(self._h, arr, len(graphs), C.c_void_p(gi.ctypes.data),
+                                            C.c_void_p(of.ctypes.data), C.c_void_p(sy.ctypes.data),
+                                            C.c_void_p(ri.ctypes.data), int(gi.shape[0]), C.byref(n)))
+        return n.value
+
+    def poll(self, max_results: int = 65536):
+        """Finished results as a numpy structured array."""
+        n = C.c_int32(0)
+        m = min(int(max_results), len(self._buf))
+        _check(lib().qec_stream_poll(self._h, self._buf, m, C.byref(n)))
+        dt = np.dtype([("request_id", "<u8"), ("obs", "<u8"), ("weight", "<i8"), ("status", "<i4"),
+                       ("graph_index", "<i4"), ("t_submit_ns", "<i8"), ("t_done_ns", "<i8")])
+        if not n.value:
+            return np.zeros(0, dt)
+        raw = C.string_at(C.addressof(self._buf), n.value * C.sizeof(qec_result))
+        return np.frombuffer(raw, dtype=dt).copy()
+
+    def flush(self):
+        _check(lib().qec_stream_flush(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().qec_stream_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def set_tuning(warps_per_block=0, blocks_per_sm=0, band_factor=0, kcap=0, max_events=0):
