@@ -186,7 +186,8 @@ int qec_get_tuning(qec_tuning *t);
  * Arguments, layouts and outputs are those of qec_decode_batch.  Limits:
  * num_shots <= QEC_STATIC_MAX_SHOTS (else QEC_ERANGE, nothing launched); a
  * shot with more than QEC_STATIC_MAX_EVENTS detection events ends with status
- * QEC_SHOT_CAPACITY.  The first call on a device looks up the array's device
+ * QEC_SHOT_CAPACITY, and so does every shot of a graph whose rows exceed
+ * QEC_STREAM_MAX_WORDS words.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  Every call shares the array and zeroes its
  * work counters on `stream`: calls whose work overlaps on the GPU race, so the

@@ -527,7 +527,11 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     const int sms = sm_count(dev);
     const int kcap = kcap_for(nmax, tune);
     SlabCaps caps = qec::caps_for_kcap(kcap);
-    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, std::min(nmax, 4 * kcap)), 2);
+    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, std::min(nmax, 4 * kcap)), 3);
+    int wmax_words = 0;
+    for (int i = 0; i < num_graphs; i++) wmax_words = std::max(wmax_words, graphs[i]->words);
+    caps.wcap = std::max(caps.wcap, wmax_words);
+    caps2.wcap = std::max(caps2.wcap, wmax_words);
     const int wpb = std::max(1, std::min(tune.warps_per_block, qec::max_block_threads() / 32));
     int bps = tune.blocks_per_sm;
     if (bps <= 0) bps = qec::occupancy_blocks(32 * wpb);

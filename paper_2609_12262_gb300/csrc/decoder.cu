@@ -96,6 +96,7 @@ struct Slab {
     int *ent;
     unsigned long long *wl0, *wl1, *tl;   // (vertex << 32 | source) work lists / new entries
     int *xsrc, *xR, *xcnt, *xcur;         // sources being extended, target radii, band counts
+    int *wcum;                            // detection events in syndrome words before word w
     // pairs: key (lo << 32 | hi), value distance, list of used slots
     unsigned long long *pkey;
     int *pval, *plist;
@@ -126,6 +127,7 @@ __host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &
     S.wl0 = bump<unsigned long long>(p, c.wc); S.wl1 = bump<unsigned long long>(p, c.wc);
     S.tl = bump<unsigned long long>(p, c.ec);
     S.xsrc = bump<int>(p, c.kc); S.xR = bump<int>(p, c.kc); S.xcnt = bump<int>(p, c.kc); S.xcur = bump<int>(p, c.kc);
+    S.wcum = bump<int>(p, c.wcap);
     S.pkey = bump<unsigned long long>(p, c.phc); S.pval = bump<int>(p, c.phc); S.plist = bump<int>(p, c.phc);
     S.y = bump<int>(p, c.nc); S.bpar = bump<int>(p, c.nc); S.label = bump<int>(p, c.nc);
     S.tpar = bump<int>(p, c.nc); S.tps = bump<int>(p, c.nc); S.tpo = bump<int>(p, c.nc);
@@ -153,6 +155,8 @@ struct Shot {
     unsigned pmask;   // pair hash mask
     int ec, wc, nc, cc;
     int band;
+    int L;                 // lookahead: explored radius >= Rad + L for every growing region
+    const unsigned *row;   // the shot's syndrome row (defect test)
     long long t;
     long long events;
     long long max_events;
@@ -268,6 +272,17 @@ __device__ void contacts_at(const Slab &S, const Shot &C, int s, int z, int base
     }
 }
 
+__device__ __forceinline__ bool is_defect(const Shot &C, int v) {
+    return (__ldg(C.row + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// Rank of detection event vertex v in the sorted event list (v must be an
+// event): events in earlier words plus set bits below v in its own word.
+__device__ __forceinline__ int rank_of(const Slab &S, const Shot &C, int v) {
+    const unsigned w = __ldg(C.row + (v >> 5));
+    return S.wcum[v >> 5] + __popc(w & ((1u << (v & 31)) - 1u));
+}
+
 __device__ __forceinline__ void bnd_update(const Slab &S, int s, int d, int eid) {
     unsigned long long v = ((unsigned long long)(unsigned)d << 32) | (unsigned)eid;
     atomicMin(&S.sbnd[s], v);
@@ -290,9 +305,20 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
     if (lane == 0) { S.ctr[C_TL] = 0; S.ctr[C_WL] = 0; }
     for (int i = lane; i < nx; i += WS) S.xcnt[i] = 0;
     __syncwarp();
-    // initial frontier: the previous band of every listed source
+    // initial frontier: the previous band of every listed source; a source
+    // never explored so far starts from its own vertex at distance 0
     for (int i = lane; i < nx; i += WS) {
         const int s = S.xsrc[i];
+        if (S.sR[s] < 0) {
+            const int v = S.svtx[s];
+            if (ht_upsert(S, C, v, s, 0) == 1) {
+                const int e = atomicAdd(&S.ctr[C_TL], 1);
+                if (e < C.ec) S.tl[e] = vs_pack(v, i); else set_err(S, ERR_CAP);
+            }
+            const int w = atomicAdd(&S.ctr[C_WL], 1);
+            if (w < C.wc) S.wl0[w] = vs_pack(v, i); else set_err(S, ERR_CAP);
+            continue;
+        }
         const int fb = S.sbeg[s], fc = S.scnt[s];
         const int base = atomicAdd(&S.ctr[C_WL], fc);
         for (int k = 0; k < fc; k++) {
@@ -366,17 +392,22 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
         S.ent[pos] = (int)(it >> 32);
     }
     __syncwarp();
-    // contacts of every new entry with the other sources' balls
+    // contacts of every new entry y of source s: other explored balls holding y
+    // (same vertex), and y being another detection event's own vertex (reach).
+    // With explored radius >= Rad + L for every growing region (L >= largest
+    // weight, >= the radius of any never-explored frozen region) these find every
+    // pair of regions at the instant they become tight: on a shortest path
+    // between them, the first vertex at distance >= Rad(a) from a lies in b's
+    // region and within Rad(a) + largest weight of a.
     for (int i = lane; i < nt; i += WS) {
         const unsigned long long it = S.tl[i];
         const int yv = (int)(it >> 32);
         const int s = S.xsrc[(int)(unsigned)(it & 0xffffffffu)];
         const int dy = ht_get(S, C, yv, s);
         contacts_at(S, C, s, yv, dy);
-        const int r0 = __ldg(g.row + yv), r1 = __ldg(g.row + yv + 1);
-        for (int j = r0; j < r1; j++) {
-            Slot sl = load_slot(g, j);
-            if (sl.nbr >= 0) contacts_at(S, C, s, sl.nbr, dy + sl.w);
+        if (yv != S.svtx[s] && is_defect(C, yv)) {
+            const int f = rank_of(S, C, yv);
+            if (f >= 0 && f != s) pair_upsert(S, C, s, f, dy);
         }
     }
     __syncwarp();
@@ -384,7 +415,7 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
 
 // Grow one source's ball by one band.  All lanes call.
 __device__ void extend_one(const Slab &S, const Shot &C, int s, int lane) {
-    if (lane == 0) { S.xsrc[0] = s; S.xR[0] = S.sR[s] + C.band; }
+    if (lane == 0) { S.xsrc[0] = s; S.xR[0] = max(S.sR[s], 0) + C.band; }
     __syncwarp();
     extend_many(S, C, 1, lane);
 }
@@ -608,11 +639,10 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
                 outer = true;
                 const int rad = S.srad[s];
                 if (!S.sexh[s]) {
-                    // due when Rad(s) reaches R_s + 1; several regions can reach it at
-                    // the same instant and are extended one after another at that time
-                    const int ahead = S.sR[s] + 1 - rad;
-                    if (ahead < 0) bad = true;
-                    best = min(best, ev_key(C.t + ahead, EV_EXTEND, s, 0));
+                    // due when Rad(s) + L would pass the explored radius; a region that
+                    // just started growing (or was never explored) is due at once
+                    const int ahead = S.sR[s] - C.L + 1 - rad;
+                    best = min(best, ev_key(C.t + (ahead > 0 ? ahead : 0), EV_EXTEND, s, 0));
                 }
                 const unsigned long long bb = __ldcg(&S.sbnd[s]);
                 if (bb != EMPTY64) {
@@ -669,10 +699,11 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
             if (lane == 0) S.ctr[C_WL] = 0;
             __syncwarp();
             for (int s = lane; s < C.K; s += WS) {
-                if (S.inplay[s] && !S.sexh[s] && S.label[S.stop[s]] == 1 && S.srad[s] == S.sR[s] + 1) {
+                const int rad = S.srad[s];
+                if (S.inplay[s] && !S.sexh[s] && S.label[S.stop[s]] == 1 && S.sR[s] - C.L + 1 - rad <= 0) {
                     const int k = atomicAdd(&S.ctr[C_WL], 1);
                     S.xsrc[k] = s;
-                    S.xR[k] = S.sR[s] + C.band;
+                    S.xR[k] = max(S.sR[s] + C.band, rad + C.L + C.band);
                 }
             }
             __syncwarp();
@@ -826,7 +857,7 @@ __device__ __forceinline__ unsigned next_pow2(unsigned x) {
 
 // Compact the set bits of the shot's syndrome row into S.svtx; returns K
 // (or -1 when K exceeds kcap).
-__device__ int load_defects(const Slab &S, const DGraph &g, const unsigned *row, int kcap, int lane) {
+__device__ int load_defects(const Slab &S, const DGraph &g, const unsigned *row, int kcap, int wcap, int lane) {
     int K = 0;
     const int nvec = g.words >> 2;
     const uint4 *rv = reinterpret_cast<const uint4 *>(row);
@@ -851,6 +882,12 @@ __device__ int load_defects(const Slab &S, const DGraph &g, const unsigned *row,
         }
         const int total = __shfl_sync(FULL, incl, WS - 1);
         int pos = K + incl - c;
+        if (i < nvec && i * 4 + 3 < wcap) {
+            S.wcum[i * 4 + 0] = pos;
+            S.wcum[i * 4 + 1] = pos + __popc(wv[0]);
+            S.wcum[i * 4 + 2] = pos + __popc(wv[0]) + __popc(wv[1]);
+            S.wcum[i * 4 + 3] = pos + __popc(wv[0]) + __popc(wv[1]) + __popc(wv[2]);
+        }
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             unsigned bits = wv[q];
@@ -867,6 +904,61 @@ __device__ int load_defects(const Slab &S, const DGraph &g, const unsigned *row,
     return K > kcap ? -1 : K;
 }
 
+constexpr int LB_CAP = 64;   // vertices one lane holds while exploring one event
+
+// Lane-local bounded Dijkstra from event s to radius Rb (one lane, no shared
+// tables): records every other event within Rb through pair_upsert (from the
+// lower-ranked end only) and the canonical boundary candidate of s.  Returns
+// the number of vertices settled, or -1 if more than LB_CAP lie within Rb.
+__device__ int local_ball(const Slab &S, const Shot &C, int s, int Rb) {
+    const DGraph &g = C.g;
+    int vv[LB_CAP], dd[LB_CAP];
+    unsigned long long fin = 0;   // settled flags
+    const int src = S.svtx[s];
+    int n = 1;
+    vv[0] = src;
+    dd[0] = 0;
+    unsigned long long bbest = EMPTY64;
+    int settled = 0;
+    for (int it = 0; it < LB_CAP; it++) {
+        int bi = -1, bd = INT_MAX;
+        for (int i = 0; i < n; i++) {
+            if (!((fin >> i) & 1ull) && dd[i] < bd) { bd = dd[i]; bi = i; }
+        }
+        if (bi < 0) break;
+        fin |= 1ull << bi;
+        settled++;
+        const int x = vv[bi], dx = bd;
+        if (x != src && is_defect(C, x)) {
+            const int f = rank_of(S, C, x);
+            if (f > s) pair_upsert(S, C, s, f, dx);
+        }
+        const int r0 = __ldg(g.row + x), r1 = __ldg(g.row + x + 1);
+        for (int j = r0; j < r1; j++) {
+            const Slot sl = load_slot(g, j);
+            const int nd = dx + sl.w;
+            if (sl.nbr < 0) {
+                const unsigned long long c = ((unsigned long long)(unsigned)nd << 32) | (unsigned)sl.eid;
+                bbest = c < bbest ? c : bbest;
+                continue;
+            }
+            if (nd > Rb) continue;
+            int k = 0;
+            while (k < n && vv[k] != sl.nbr) k++;
+            if (k < n) {
+                if (!((fin >> k) & 1ull) && nd < dd[k]) dd[k] = nd;
+            } else {
+                if (n == LB_CAP) return -1;
+                vv[n] = sl.nbr;
+                dd[n] = nd;
+                n++;
+            }
+        }
+    }
+    atomicMin(&S.sbnd[s], bbest);
+    return settled;
+}
+
 // Decode one shot with hash tables scaled by `scale`; returns QEC_SHOT_* or -1
 // when the working set overflowed (retry with a larger scale).
 __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
@@ -879,16 +971,20 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     C.events = 0;
     C.t = 0;
     C.deadline = deadline;
-    const int K = load_defects(S, g, row, A.caps.kc, lane);
+    C.row = row;
+    C.L = max(g.wmax, (g.b1 + 1) / 2) + 1;
+    if (g.words > A.caps.wcap) return -2;
+    const int K = load_defects(S, g, row, A.caps.kc, A.caps.wcap, lane);
     if (K < 0) return -2;
     C.K = K;
     C.max_events = min(A.max_events, 256LL * K + 4096);
     if (K == 0) { w_out = 0; o_out = 0; return QEC_SHOT_OK; }
     if (K > ID_MAX - 1 || 2 * K + 8 > A.caps.nc) return -2;
     C.nc = min(A.caps.nc, 2 * K + 16);   // leaves + at most K blossoms alive at once
-    // about 7 explored entries and 1 pair per detection event at the design
-    // point; the tables stay at most half full or the shot is retried larger
-    const unsigned hs = min(next_pow2(max(128u, 32u * (unsigned)K * scale)), (unsigned)A.caps.hc);
+    // about 7 (at most ~25) explored entries and 1 (at most ~2) pair per
+    // detection event at the design point; the tables stay at most half full or
+    // the shot is retried larger
+    const unsigned hs = min(next_pow2(max(128u, 64u * (unsigned)K * scale)), (unsigned)A.caps.hc);
     const unsigned ps = min(next_pow2(max(64u, 8u * (unsigned)K * scale)), (unsigned)A.caps.phc);
     C.hmask = hs - 1;
     C.pmask = ps - 1;
@@ -896,8 +992,8 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     // sources, leaf nodes, free list
     int nhi = K;
     for (int s = lane; s < K; s += WS) {
-        S.srad[s] = 0; S.sR[s] = 0; S.scnt[s] = 1; S.sbeg[s] = s; S.sexh[s] = 0; S.inplay[s] = 0;
-        S.sbnd[s] = EMPTY64; S.ent[s] = S.svtx[s];
+        S.srad[s] = 0; S.sR[s] = -1; S.scnt[s] = 0; S.sbeg[s] = 0; S.sexh[s] = 0; S.inplay[s] = 0;
+        S.sbnd[s] = EMPTY64;
         S.alive[s] = 0; S.y[s] = 0; S.bpar[s] = -1; S.label[s] = 0; S.tpar[s] = -1;
         S.mate[s] = MATE_NONE; S.nroot[s] = -1; S.stop[s] = s; S.minleaf[s] = s; S.clen[s] = 0;
     }
@@ -907,28 +1003,29 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
         S.freel[i] = v;
         S.alive[v] = 0; S.clen[v] = 0; S.bpar[v] = -1;
     }
-    if (lane == 0) { S.ctr[C_ECOUNT] = K; S.ctr[C_NFREE] = nfree; }
+    if (lane == 0) { S.ctr[C_ECOUNT] = 0; S.ctr[C_NFREE] = nfree; }
     __syncwarp();
+    // ---- Algorithm 1, level 1: every event's neighbourhood within b_1 by a
+    // lane-local Dijkstra (each lane its own events): pairs within b_1 with their
+    // exact distance (found by reaching the other event's vertex) and the
+    // canonical boundary candidate.  Events whose neighbourhood is too large for
+    // the lane go through the warp-wide flooder instead.
+    bool any_big = false;
     for (int s = lane; s < K; s += WS) {
-        int f = ht_upsert(S, C, S.svtx[s], s, 0);
-        (void)f;
+        const int r = local_ball(S, C, s, g.b1);
+        if (r < 0) { S.cst0[s] = 1; any_big = true; } else S.cst0[s] = 0;
     }
     __syncwarp();
-    // contacts between adjacent sources at t = 0
-    for (int s = lane; s < K; s += WS) {
-        const int v = S.svtx[s];
-        const int r0 = __ldg(g.row + v), r1 = __ldg(g.row + v + 1);
-        for (int j = r0; j < r1; j++) {
-            Slot sl = load_slot(g, j);
-            if (sl.nbr >= 0) contacts_at(S, C, s, sl.nbr, sl.w);
+    if (__any_sync(FULL, any_big)) {
+        if (lane == 0) {
+            int k = 0;
+            for (int s = 0; s < K; s++)
+                if (S.cst0[s]) { S.xsrc[k] = s; S.xR[k] = max(g.b1, C.band); k++; }
+            S.ctr[C_WL] = k;
         }
+        __syncwarp();
+        extend_many(S, C, __ldcg(&S.ctr[C_WL]), lane);
     }
-    __syncwarp();
-    // ---- Algorithm 1, level 1: balls of radius max(b1/2, band) around every event
-    const int R1 = max(g.b1 / 2, C.band);
-    for (int s = lane; s < K; s += WS) { S.xsrc[s] = s; S.xR[s] = R1; }
-    __syncwarp();
-    extend_many(S, C, K, lane);
     {
         const int err = __ldcg(&S.ctr[C_ERR]);
         if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
@@ -1115,8 +1212,9 @@ SlabCaps caps_for_kcap(int kcap, int table_factor) {
     c.hc = p2(64LL * f * kcap < 1024 ? 1024 : 64LL * f * kcap);
     c.ec = (int)(48 * f * kcap + 64);
     c.wc = (int)(48 * f * kcap + 64);
-    c.phc = p2(16LL * f * kcap < 256 ? 256 : 16LL * f * kcap);
+    c.phc = p2(16LL * f * f * kcap < 256 ? 256 : 16LL * f * f * kcap);   // dense shots: pairs grow ~ f^2
     c.nc = 2 * kcap + 16;
+    c.wcap = QEC_STREAM_MAX_WORDS;   // rows up to 73,728 detectors; callers raise it for larger graphs
     c.cc = 24 * kcap + 64;
     return c;
 }

@@ -41,6 +41,7 @@ struct SlabCaps {
     int phc;   // pair hash slots (power of two)
     int nc;    // matcher nodes
     int cc;    // blossom cycle pool
+    int wcap;  // syndrome words per row
 };
 
 struct BatchArgs {

@@ -179,3 +179,33 @@ def test_autotuner_candidates_agree_and_match_oracle(qd):
         qd.set_tuning(warps_per_block=-1, blocks_per_sm=-1, band_factor=-1, kcap=-1)
     rows = [syn[offs[s]:offs[s] + graphs[gid[s]].words] for s in range(gid.shape[0])]
     assert_same(gpu, oracle_decode(graphs, gid, rows), "autotuned")
+
+
+def test_dense_graphs_overflow_the_lane_local_search(qd):
+    """High-degree random graphs with narrow weights: many events have more
+    vertices within b_1 than one lane holds, which sends them through the
+    warp-wide flooder; observables on internal edges exercise path tracing."""
+    rng = np.random.default_rng(3)
+    for trial in range(3):
+        n = 120
+        u, v = [], []
+        for x in range(n - 1):
+            u.append(x); v.append(x + 1)
+        for _ in range(n * 8):
+            a, b = int(rng.integers(0, n)), int(rng.integers(-1, n))
+            if a != b:
+                u.append(a); v.append(b)
+        w = rng.integers(3, 9, size=len(u)).astype(np.int32)
+        o = (rng.random(len(u)) < 0.3).astype(np.uint64)
+
+        class PG:
+            pass
+        pg = PG()
+        pg.num_detectors, pg.u, pg.v, pg.w, pg.obs = n, np.array(u, np.int32), np.array(v, np.int32), w, o
+        g = qd.Graph(n, pg.u, pg.v, w, o)
+        rows = [pack_defects(sorted(set(rng.integers(0, n, size=int(rng.integers(0, 30))).tolist())), n)
+                for _ in range(300)]
+        syn = np.stack(rows)
+        gpu = gpu_decode(qd, g, syn)
+        ref = oracle_decode([pg], np.zeros(syn.shape[0], np.int32), list(syn), workers=1)
+        assert_same(gpu, ref, "dense graph %d" % trial)
