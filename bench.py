@@ -61,6 +61,11 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--serve-seconds", type=float, default=2.5, help="serving run length (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200000.0, help="Poisson arrival rate, windows/s")
+    ap.add_argument("--scaling", action="store_true",
+                    help="scaling study: d in {25,31,41,51} x p in {.001,.003,.005}, us per round vs d")
+    ap.add_argument("--scaling-shots", type=int, default=10000)
+    ap.add_argument("--scaling-check", type=int, default=0, help="windows per point checked against the oracle")
+    ap.add_argument("--scaling-save", default="", help="directory for the first outputs of every point")
     return ap.parse_args()
 
 
@@ -68,7 +73,8 @@ DS = [7, 9, 11, 13, 15, 17, 19, 21]
 
 
 def workload(args, rank):
-    graphs, gid, offs, syn = mixed_batch(DS, args.shots_per_d, args.p, seed=args.seed + 1000 * rank)
+    from paper_2609_12262_gb300.replicas import shard_seed
+    graphs, gid, offs, syn = mixed_batch(DS, args.shots_per_d, args.p, seed=shard_seed(args.seed, rank))
     return graphs, gid, offs, syn
 
 
@@ -144,10 +150,8 @@ class Clocks:
 
 
 def dist_setup():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2609_12262_gb300.replicas import world
+    return world()
 
 
 def cpu_oracle_rate(graphs, gid, offs, syn, seconds, workers=None):
@@ -227,6 +231,66 @@ def serving_run(q, args, dev):
             "latency": "result available on the host minus the scheduled Poisson arrival"}
 
 
+def scaling_study(q, args, dev):
+    """Large single windows: throughput and single-window latency per (d, p)."""
+    import torch
+    rows = []
+    for d in (25, 31, 41, 51):
+        for p in (0.001, 0.003, 0.005):
+            pg = rotated_surface_code(d, d, p)
+            syn, _ = sample_shots(pg, args.scaling_shots, args.seed + d * 1000 + int(p * 1e4))
+            pc = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)
+            kmax = int(pc.max())
+            g = q.Graph.from_phys(pg)
+            q.set_tuning(kcap=max(64, int(kmax * 1.1) + 8), blocks_per_sm=-1, warps_per_block=-1)
+            t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
+            S = syn.shape[0]
+            out = (torch.empty(S, dtype=torch.int64, device=dev), torch.empty(S, dtype=torch.int64, device=dev),
+                   torch.empty(S, dtype=torch.int32, device=dev))
+            q.decode_batch([g], t, num_shots=S, out=out)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            q.decode_batch([g], t, num_shots=S, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            st = out[2].cpu().numpy()
+            # single-window latency: one window per launch
+            nl = min(16, S)
+            po = (torch.empty(nl, dtype=torch.int64, device=dev), torch.empty(nl, dtype=torch.int64, device=dev),
+                  torch.empty(nl, dtype=torch.int32, device=dev))
+            q.decode_plain(g, t, num_shots=nl, out=po)
+            torch.cuda.synchronize()
+            a.record()
+            q.decode_plain(g, t, num_shots=nl, out=po)
+            b.record()
+            torch.cuda.synchronize()
+            lat_ms = a.elapsed_time(b) / nl
+            row = {"d": d, "rounds": d, "p": p, "windows": S, "mean_events": float(pc.mean()), "max_events": kmax,
+                   "batch_ms": ms, "windows_per_s": S / (ms / 1e3), "us_per_round_throughput": ms * 1e3 / S / d,
+                   "window_latency_us": lat_ms * 1e3, "us_per_round_latency": lat_ms * 1e3 / d,
+                   "nonzero_status": int(np.count_nonzero(st))}
+            if args.scaling_save:
+                os.makedirs(args.scaling_save, exist_ok=True)
+                k = min(64, S)
+                np.savez(os.path.join(args.scaling_save, "d%d_p%g.npz" % (d, p)), weight=out[1].cpu().numpy()[:k],
+                         obs=q.to_uint64(out[0])[:k], status=st[:k], seed=args.seed + d * 1000 + int(p * 1e4))
+            if args.scaling_check > 0:
+                sys.path.insert(0, os.path.join(ROOT, "tests"))
+                from oracle_pool import oracle_decode
+                k = min(args.scaling_check, S)
+                rw, ro, rs = oracle_decode([pg], np.zeros(k, np.int32), list(syn[:k]))
+                gw, go = out[1].cpu().numpy()[:k], q.to_uint64(out[0])[:k]
+                row["oracle_checked"] = k
+                row["oracle_mismatch"] = int(np.count_nonzero((rw != gw) | (ro != go) | (rs != st[:k])))
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            del t, out
+    q.set_tuning(kcap=-1, blocks_per_sm=-1, warps_per_block=-1)
+    return rows
+
+
 def reference_arm(args, ws, rank):
     if ws > 1 and rank != 0:
         return
@@ -287,6 +351,9 @@ def main():
     import paper_2609_12262_gb300 as q
     if args.kcap:
         q.set_tuning(kcap=args.kcap)
+    if args.scaling:
+        scaling_study(q, args, torch.device("cuda", local))
+        return
 
     graphs, gid, offs, syn = workload(args, rank)
     S = int(gid.shape[0])
@@ -335,9 +402,8 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     if dist is not None:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        from paper_2609_12262_gb300.replicas import max_over_ranks
+        total_ms = max_over_ranks(total_ms, dev)
     clocks = clk.summary()
     ms_step = total_ms / args.steps
     value = ws * S / (ms_step / 1000.0)
@@ -397,9 +463,8 @@ def main():
         barrier()
         e_ms = a.elapsed_time(b) / args.steps
         if dist is not None:
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
+            from paper_2609_12262_gb300.replicas import max_over_ranks
+            e_ms = max_over_ranks(e_ms, dev)
         h2d = int(h_syn.numel() * 4 + h_gid.numel() * 4 + h_off.numel() * 8)
         d2h = int(S * (8 + 8 + 4))
         e2e = {"value": ws * S / (e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,

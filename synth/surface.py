@@ -158,14 +158,18 @@ def _sample_flips(rng, pe: np.ndarray, shots: int):
     return r, c
 
 
-def sample_shots(g: PhysGraph, shots: int, seed: int, chunk: int = 8192):
+def sample_shots(g: PhysGraph, shots: int, seed: int, chunk: int | None = None):
     """Sample `shots` syndromes.
 
     Returns (syndromes uint32 [shots, g.words], true_obs uint64 [shots]).
     Chunk c of the shots draws from numpy Philox(key=seed, counter=c), so the
-    output depends only on (seed, shots, chunk).
+    output depends only on (seed, shots, chunk).  The default chunk is 8192
+    shots, fewer for graphs above 8192 detectors (2^26 / detectors, at least 64)
+    so one chunk's per-detector counters stay near 512 MB.
     """
     n = g.num_detectors
+    if chunk is None:
+        chunk = max(64, min(8192, (1 << 26) // max(n, 1)))
     out = np.zeros((shots, g.words), dtype=np.uint32)
     true_obs = np.zeros(shots, dtype=np.uint64)
     for c0 in range(0, shots, chunk):

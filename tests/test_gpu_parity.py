@@ -209,3 +209,15 @@ def test_dense_graphs_overflow_the_lane_local_search(qd):
         gpu = gpu_decode(qd, g, syn)
         ref = oracle_decode([pg], np.zeros(syn.shape[0], np.int32), list(syn), workers=1)
         assert_same(gpu, ref, "dense graph %d" % trial)
+
+
+@pytest.mark.parametrize("d,p,shots", [(25, 0.005, 6), (31, 0.003, 4), (41, 0.001, 3), (51, 0.001, 2)])
+def test_large_windows_match_oracle(qd, d, p, shots):
+    """Full-size single windows of the scaling study (hundreds of detection
+    events per window) against the oracle, in the main batched path."""
+    pg = rotated_surface_code(d, d, p)
+    g = qd.Graph.from_phys(pg)
+    syn, _ = sample_shots(pg, shots, 1000 + d)
+    gpu = gpu_decode(qd, g, syn)
+    ref = oracle_decode([pg], np.zeros(shots, np.int32), list(syn), chunk=1)
+    assert_same(gpu, ref, "d%d p%g" % (d, p))
