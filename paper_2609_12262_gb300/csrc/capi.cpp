@@ -32,6 +32,7 @@ struct qec_graph {
     std::vector<unsigned long long> eobs;
     int *d_row = nullptr;
     Slot *d_slot = nullptr;
+    int *d_seid = nullptr;
     unsigned long long *d_eobs = nullptr;
     int2 *d_eend = nullptr;
     DGraph dg{};
@@ -195,6 +196,8 @@ struct Workspace {
     SlabCaps caps2{};
     unsigned long long *queue = nullptr;
     int *overflow = nullptr;
+    int *order = nullptr;          // graph-sorted work order of a mixed batch
+    int *gcnt = nullptr;           // 64 ints: per-graph counts and cursors
     long long overflow_cap = 0;
     cudaEvent_t done = nullptr;
     std::mutex mu;
@@ -209,10 +212,14 @@ void ws_free(Workspace &w) {
     if (w.slabs2) cudaFree(w.slabs2);
     if (w.queue) cudaFree(w.queue);
     if (w.overflow) cudaFree(w.overflow);
+    if (w.order) cudaFree(w.order);
+    if (w.gcnt) cudaFree(w.gcnt);
     if (w.done) cudaEventDestroy(w.done);
     w.slabs = w.slabs2 = nullptr;
     w.queue = nullptr;
     w.overflow = nullptr;
+    w.order = nullptr;
+    w.gcnt = nullptr;
     w.done = nullptr;
     w.slab_bytes = w.slab_bytes2 = 0;
     w.nwarps = w.nwarps2 = 0;
@@ -270,9 +277,13 @@ int ws_ensure(Workspace &w, int dev, const SlabCaps &caps, long long nwarps, con
             if (e != cudaSuccess) return fail(QEC_ENOMEM, "workspace allocation failed");
         }
         if (w.overflow) cudaFree(w.overflow);
+        if (w.order) cudaFree(w.order);
         w.overflow = nullptr;
+        w.order = nullptr;
         long long cap = std::max<long long>(nshots, 1024);
         e = cudaMalloc(&w.overflow, (size_t)cap * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&w.order, (size_t)cap * sizeof(int));
+        if (e == cudaSuccess && !w.gcnt) e = cudaMalloc(&w.gcnt, 64 * sizeof(int));
         if (e != cudaSuccess) { w.overflow_cap = 0; return fail(QEC_ENOMEM, "workspace allocation failed"); }
         w.overflow_cap = cap;
     }
@@ -392,12 +403,19 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
     }
     for (int x = 0; x < n; x++) row[x + 1] += row[x];
     std::vector<Slot> slots((size_t)row[n] + 1);
+    std::vector<int> seid((size_t)row[n] + 1, -1);
     std::vector<int> fill((size_t)n, 0);
     std::vector<int2> eend((size_t)g->m + 1);
     for (int e = 0; e < g->m; e++) {
         const int a = g->eu[e], b = g->ev[e];
-        slots[row[a] + fill[a]++] = Slot{b, g->ew[e], e, 0};
-        if (b >= 0) slots[row[b] + fill[b]++] = Slot{a, g->ew[e], e, 0};
+        const int ja = row[a] + fill[a]++;
+        slots[ja] = Slot{b >= 0 ? b : -1 - e, g->ew[e]};
+        seid[ja] = e;
+        if (b >= 0) {
+            const int jb = row[b] + fill[b]++;
+            slots[jb] = Slot{a, g->ew[e]};
+            seid[jb] = e;
+        }
         eend[e] = make_int2(a, g->ew[e]);
     }
     cudaError_t ce = cudaGetDevice(&g->device);
@@ -407,6 +425,7 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
     if (ce == cudaSuccess) ce = cudaMalloc(&g->d_slot, sizeof(Slot) * nslots);
     if (ce == cudaSuccess) ce = cudaMalloc(&g->d_eobs, sizeof(unsigned long long) * ne);
     if (ce == cudaSuccess) ce = cudaMalloc(&g->d_eend, sizeof(int2) * ne);
+    if (ce == cudaSuccess) ce = cudaMalloc(&g->d_seid, sizeof(int) * nslots);
     if (ce != cudaSuccess) { qec_graph_destroy(g); return fail(QEC_ENOMEM, "device allocation failed"); }
     std::vector<unsigned long long> eo(g->eobs);
     eo.push_back(0);
@@ -414,6 +433,7 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
     if (ce == cudaSuccess) ce = cudaMemcpy(g->d_slot, slots.data(), sizeof(Slot) * nslots, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(g->d_eobs, eo.data(), sizeof(unsigned long long) * ne, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(g->d_eend, eend.data(), sizeof(int2) * ne, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(g->d_seid, seid.data(), sizeof(int) * nslots, cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) { qec_graph_destroy(g); return cuda_fail(ce, "cudaMemcpy"); }
     DGraph &d = g->dg;
     d.n = n;
@@ -426,6 +446,7 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
     d.slot = g->d_slot;
     d.eobs = g->d_eobs;
     d.eend = g->d_eend;
+    d.seid = g->d_seid;
     *out = g;
     return QEC_OK;
 }
@@ -436,6 +457,7 @@ int qec_graph_destroy(qec_graph *g) {
     if (g->d_slot) cudaFree(g->d_slot);
     if (g->d_eobs) cudaFree(g->d_eobs);
     if (g->d_eend) cudaFree(g->d_eend);
+    if (g->d_seid) cudaFree(g->d_seid);
     delete g;
     return QEC_OK;
 }
@@ -574,6 +596,17 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
         a.single_shot = -1;
         ce = qec::launch_reset_queue(w.queue, s);
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemsetAsync");
+        if (num_graphs > 1 && graph_of_shot) {
+            // shots grouped by graph, largest graphs first, so concurrent warps
+            // share one graph's lines in cache and the longest shots do not trail
+            int gorder[QEC_MAX_GRAPHS_PER_BATCH];
+            for (int i = 0; i < num_graphs; i++) gorder[i] = i;
+            std::stable_sort(gorder, gorder + num_graphs,
+                             [&](int x, int y) { return graphs[x]->n > graphs[y]->n; });
+            ce = qec::launch_graph_sort(graph_of_shot, num_shots, num_graphs, gorder, w.gcnt, w.order, s);
+            if (ce != cudaSuccess) return cuda_fail(ce, "graph sort launch");
+            a.order = w.order;
+        }
         a.slabs = w.slabs;
         a.slab_bytes = w.slab_bytes;
         a.caps = w.caps;

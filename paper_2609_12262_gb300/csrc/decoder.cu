@@ -35,6 +35,7 @@
 // Every loop is bounded: the event budget, hash probe lengths and list
 // capacities end a shot with a status code instead of spinning.
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -69,6 +70,31 @@ __device__ __forceinline__ unsigned long long ev_key(long long t, int kind, int 
     t = t < T_MAX ? t : T_MAX;
     return ((unsigned long long)t << 38) | ((unsigned long long)kind << 36) |
            ((unsigned long long)lo << 18) | (unsigned long long)hi;
+}
+
+// Loads of per-shot state written by other lanes of this warp (plain stores or
+// atomics): relaxed at CTA scope, so they may hit L1 and still observe every
+// write ordered before them by the warp's __syncwarp barriers.
+__device__ __forceinline__ int ldr(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.cta.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ldr(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.cta.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Warp-aggregated atomicAdd(ctr, 1) over the currently active lanes.
+__device__ __forceinline__ int agg_inc(int *ctr, int lane) {
+    const unsigned m = __activemask();
+    const int leader = __ffs(m) - 1;
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(ctr, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    return base + rank;
 }
 
 __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
@@ -177,8 +203,8 @@ __device__ int ht_get(const Slab &S, const Shot &C, int v, int s) {
     const unsigned long long key = ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
     unsigned i = hslot(v, C.hmask);
     for (unsigned n = 0; n <= C.hmask; n++) {
-        unsigned long long k = __ldcg(&S.hkey[i]);
-        if (k == key) return __ldcg(&S.hval[i]);
+        unsigned long long k = ldr(&S.hkey[i]);
+        if (k == key) return ldr(&S.hval[i]);
         if (k == EMPTY64) return INF32;
         i = (i + 1) & C.hmask;
     }
@@ -190,13 +216,11 @@ __device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d) {
     const unsigned long long key = ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
     unsigned i = hslot(v, C.hmask);
     for (unsigned n = 0; n <= C.hmask; n++) {
-        unsigned long long k = __ldcg(&S.hkey[i]);
+        unsigned long long k = ldr(&S.hkey[i]);
         if (k == EMPTY64) {
             unsigned long long prev = atomicCAS(&S.hkey[i], EMPTY64, key);
             if (prev == EMPTY64) {
                 atomicMin(&S.hval[i], d);
-                int f = atomicAdd(&S.ctr[C_HFILL], 1);
-                if ((unsigned)f * 2u > C.hmask) set_err(S, ERR_CAP);
                 return 1;
             }
             k = prev;
@@ -216,7 +240,7 @@ __device__ void pair_upsert(const Slab &S, const Shot &C, int a, int b, int d) {
     const unsigned long long key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
     unsigned i = pslot(lo, hi, C.pmask);
     for (unsigned n = 0; n <= C.pmask; n++) {
-        unsigned long long k = __ldcg(&S.pkey[i]);
+        unsigned long long k = ldr(&S.pkey[i]);
         if (k == EMPTY64) {
             unsigned long long prev = atomicCAS(&S.pkey[i], EMPTY64, key);
             if (prev == EMPTY64) {
@@ -242,18 +266,26 @@ __device__ int pair_get(const Slab &S, const Shot &C, int a, int b) {
     const unsigned long long key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
     unsigned i = pslot(lo, hi, C.pmask);
     for (unsigned n = 0; n <= C.pmask; n++) {
-        unsigned long long k = __ldcg(&S.pkey[i]);
-        if (k == key) return __ldcg(&S.pval[i]);
+        unsigned long long k = ldr(&S.pkey[i]);
+        if (k == key) return ldr(&S.pval[i]);
         if (k == EMPTY64) return INF32;
         i = (i + 1) & C.pmask;
     }
     return INF32;
 }
 
-__device__ __forceinline__ Slot load_slot(const DGraph &g, int j) {
-    int4 v = __ldg(reinterpret_cast<const int4 *>(g.slot) + j);
-    Slot s;
-    s.nbr = v.x; s.w = v.y; s.eid = v.z; s.pad = v.w;
+struct SlotV {
+    int nbr;   // neighbour detector, -1 for the boundary
+    int w;     // internal weight
+    int eid;   // merged edge id (boundary slots only; -1 otherwise)
+};
+
+__device__ __forceinline__ SlotV load_slot(const DGraph &g, int j) {
+    const int2 v = __ldg(reinterpret_cast<const int2 *>(g.slot) + j);
+    SlotV s;
+    s.w = v.y;
+    if (v.x < 0) { s.nbr = -1; s.eid = -1 - v.x; }
+    else { s.nbr = v.x; s.eid = -1; }
     return s;
 }
 
@@ -262,11 +294,11 @@ __device__ __forceinline__ Slot load_slot(const DGraph &g, int j) {
 __device__ void contacts_at(const Slab &S, const Shot &C, int s, int z, int base) {
     unsigned i = hslot(z, C.hmask);
     for (unsigned n = 0; n <= C.hmask; n++) {
-        unsigned long long k = __ldcg(&S.hkey[i]);
+        unsigned long long k = ldr(&S.hkey[i]);
         if (k == EMPTY64) return;
         if ((int)(k >> 32) == z) {
             int s2 = (int)(unsigned)(k & 0xffffffffu);
-            if (s2 != s) pair_upsert(S, C, s, s2, base + __ldcg(&S.hval[i]));
+            if (s2 != s) pair_upsert(S, C, s, s2, base + ldr(&S.hval[i]));
         }
         i = (i + 1) & C.hmask;
     }
@@ -327,7 +359,7 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
         }
     }
     __syncwarp();
-    int nf = min(__ldcg(&S.ctr[C_WL]), C.wc);
+    int nf = min(ldr(&S.ctr[C_WL]), C.wc);
     unsigned long long *F = S.wl0, *Wn = S.wl1;
     for (int iter = 0;; iter++) {
         if (iter >= 4096) { if (lane == 0) set_err(S, ERR_INTERNAL); break; }
@@ -342,32 +374,33 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
             const int dx = ht_get(S, C, x, s);
             const int r0 = __ldg(g.row + x), r1 = __ldg(g.row + x + 1);
             for (int j = r0; j < r1; j++) {
-                Slot sl = load_slot(g, j);
+                SlotV sl = load_slot(g, j);
                 const int nd = dx + sl.w;
                 if (sl.nbr < 0) { bnd_update(S, s, nd, sl.eid); continue; }
                 if (nd > Rn) continue;
                 int r = ht_upsert(S, C, sl.nbr, s, nd);
                 if (r == 1) {
-                    const int e = atomicAdd(&S.ctr[C_TL], 1);
+                    const int e = agg_inc(&S.ctr[C_TL], lane);
                     if (e < C.ec) S.tl[e] = vs_pack(sl.nbr, xi); else set_err(S, ERR_CAP);
                 }
                 if (r >= 1) {
-                    const int w = atomicAdd(&S.ctr[C_WL], 1);
+                    const int w = agg_inc(&S.ctr[C_WL], lane);
                     if (w < C.wc) Wn[w] = vs_pack(sl.nbr, xi); else set_err(S, ERR_CAP);
                 }
             }
         }
         __syncwarp();
-        const int nw = __ldcg(&S.ctr[C_WL]);
-        const int err = __ldcg(&S.ctr[C_ERR]);
+        const int nw = ldr(&S.ctr[C_WL]);
+        const int err = ldr(&S.ctr[C_ERR]);
         if (nw == 0 || err) break;
         nf = min(nw, C.wc);
         unsigned long long *t = F; F = Wn; Wn = t;
     }
     __syncwarp();
-    const int nt = min(__ldcg(&S.ctr[C_TL]), C.ec);
-    const int e0 = __ldcg(&S.ctr[C_ECOUNT]);
-    if (e0 + nt > C.ec) { if (lane == 0) set_err(S, ERR_CAP); __syncwarp(); return; }
+    const int nt = min(ldr(&S.ctr[C_TL]), C.ec);
+    const int e0 = ldr(&S.ctr[C_ECOUNT]);
+    // explored-entry table at most half full, list room left
+    if (e0 + nt > C.ec || (unsigned)(e0 + nt) * 2u > C.hmask) { if (lane == 0) set_err(S, ERR_CAP); __syncwarp(); return; }
     // bands made contiguous per source (counting sort of the new entries)
     for (int i = lane; i < nt; i += WS) atomicAdd(&S.xcnt[(int)(unsigned)(S.tl[i] & 0xffffffffu)], 1);
     __syncwarp();
@@ -644,7 +677,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
                     const int ahead = S.sR[s] - C.L + 1 - rad;
                     best = min(best, ev_key(C.t + (ahead > 0 ? ahead : 0), EV_EXTEND, s, 0));
                 }
-                const unsigned long long bb = __ldcg(&S.sbnd[s]);
+                const unsigned long long bb = ldr(&S.sbnd[s]);
                 if (bb != EMPTY64) {
                     const int bd = (int)(bb >> 32);
                     if (bd < rad) bad = true;
@@ -654,17 +687,17 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
                 inner_leaf_min = min(inner_leaf_min, S.y[s]);
             }
         }
-        const int np = __ldcg(&S.ctr[C_NPAIRS]);
+        const int np = ldr(&S.ctr[C_NPAIRS]);
         for (int i = lane; i < np; i += WS) {
             const int sl = S.plist[i];
-            const unsigned long long k = __ldcg(&S.pkey[sl]);
+            const unsigned long long k = ldr(&S.pkey[sl]);
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
             if (!S.inplay[a] || !S.inplay[b]) continue;
             const int A = S.stop[a], B = S.stop[b];
             if (A == B) continue;
             const int r = S.label[A] + S.label[B];
             if (r <= 0) continue;
-            const int gap = __ldcg(&S.pval[sl]) - S.srad[a] - S.srad[b];
+            const int gap = ldr(&S.pval[sl]) - S.srad[a] - S.srad[b];
             if (gap < 0 || gap % r) { bad = true; continue; }
             best = min(best, ev_key(C.t + gap / r, EV_COLLIDE, a, b));
         }
@@ -707,7 +740,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
                 }
             }
             __syncwarp();
-            extend_many(S, C, __ldcg(&S.ctr[C_WL]), lane);
+            extend_many(S, C, ldr(&S.ctr[C_WL]), lane);
         } else if (kind == EV_IMPLODE) {
             ev_shatter(S, C, S.stop[lo], lane);
         } else if (kind == EV_BOUNDARY) {
@@ -729,7 +762,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
                 return RUN_INTERNAL;
             }
         }
-        const int err = __ldcg(&S.ctr[C_ERR]);
+        const int err = ldr(&S.ctr[C_ERR]);
         if (err) return (err & ERR_INTERNAL) ? RUN_INTERNAL : RUN_CAP;
     }
 }
@@ -738,7 +771,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
 // distance dx: predecessor = lowest edge id among tight edges.  All lanes call.
 __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int dx, int lane) {
     const DGraph &g = C.g;
-    for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s] && !__ldcg(&S.ctr[C_ERR]); n++) extend_one(S, C, s, lane);
+    for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]); n++) extend_one(S, C, s, lane);
     unsigned long long o = 0;
     const int src = S.svtx[s];
     int cur = x, dcur = dx;
@@ -746,11 +779,11 @@ __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int
         const int r0 = __ldg(g.row + cur), r1 = __ldg(g.row + cur + 1);
         unsigned long long best = EMPTY64;
         for (int j = r0 + lane; j < r1; j += WS) {
-            Slot sl = load_slot(g, j);
+            SlotV sl = load_slot(g, j);
             if (sl.nbr < 0) continue;
             const int dy = ht_get(S, C, sl.nbr, s);
             if (dy != INF32 && dy + sl.w == dcur)
-                best = min(best, ((unsigned long long)(unsigned)sl.eid << 32) | (unsigned)sl.nbr);
+                best = min(best, ((unsigned long long)(unsigned)__ldg(g.seid + j) << 32) | (unsigned)sl.nbr);
         }
         best = warp_min64(best);
         if (best == EMPTY64) { if (lane == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
@@ -811,7 +844,7 @@ __device__ void trace(const Slab &S, Shot &C, int lane, int nhi, long long &wint
         const int a = S.tmpa[i], b = S.tmpb[i];
         if (a < 0 || a >= C.K || b >= C.K) { set_err(S, ERR_INTERNAL); continue; }
         if (b < 0) {
-            const unsigned long long bb = __ldcg(&S.sbnd[a]);
+            const unsigned long long bb = ldr(&S.sbnd[a]);
             if (bb == EMPTY64) { set_err(S, ERR_INTERNAL); continue; }
             w += (long long)(bb >> 32);
             o ^= __ldg(C.g.eobs + (int)(unsigned)(bb & 0xffffffffu));
@@ -824,12 +857,12 @@ __device__ void trace(const Slab &S, Shot &C, int lane, int nhi, long long &wint
     w = warp_sum64(w);
 #pragma unroll
     for (int off = WS / 2; off; off >>= 1) o ^= __shfl_xor_sync(FULL, o, off);
-    if (C.g.internal_obs && !__ldcg(&S.ctr[C_ERR])) {
+    if (C.g.internal_obs && !ldr(&S.ctr[C_ERR])) {
         // detector-detector edges carry observables: walk the canonical paths
         for (int i = 0; i < np; i++) {
             const int a = S.tmpa[i], b = S.tmpb[i];
             if (b < 0) {
-                const unsigned long long bb = __ldcg(&S.sbnd[a]);
+                const unsigned long long bb = ldr(&S.sbnd[a]);
                 const int e = (int)(unsigned)(bb & 0xffffffffu);
                 const int2 ue = __ldg(C.g.eend + e);
                 o ^= path_obs(S, C, a, ue.x, (int)(bb >> 32) - ue.y, lane);
@@ -922,9 +955,8 @@ __device__ int local_ball(const Slab &S, const Shot &C, int s, int Rb) {
     int settled = 0;
     for (int it = 0; it < LB_CAP; it++) {
         int bi = -1, bd = INT_MAX;
-        for (int i = 0; i < n; i++) {
+        for (int i = 0; i < n; i++)
             if (!((fin >> i) & 1ull) && dd[i] < bd) { bd = dd[i]; bi = i; }
-        }
         if (bi < 0) break;
         fin |= 1ull << bi;
         settled++;
@@ -935,7 +967,7 @@ __device__ int local_ball(const Slab &S, const Shot &C, int s, int Rb) {
         }
         const int r0 = __ldg(g.row + x), r1 = __ldg(g.row + x + 1);
         for (int j = r0; j < r1; j++) {
-            const Slot sl = load_slot(g, j);
+            const SlotV sl = load_slot(g, j);
             const int nd = dx + sl.w;
             if (sl.nbr < 0) {
                 const unsigned long long c = ((unsigned long long)(unsigned)nd << 32) | (unsigned)sl.eid;
@@ -981,11 +1013,11 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     if (K == 0) { w_out = 0; o_out = 0; return QEC_SHOT_OK; }
     if (K > ID_MAX - 1 || 2 * K + 8 > A.caps.nc) return -2;
     C.nc = min(A.caps.nc, 2 * K + 16);   // leaves + at most K blossoms alive at once
-    // about 7 (at most ~25) explored entries and 1 (at most ~2) pair per
+    // about 8 (rarely ~15) explored entries and 1 (at most ~2) pair per
     // detection event at the design point; the tables stay at most half full or
-    // the shot is retried larger
-    const unsigned hs = min(next_pow2(max(128u, 64u * (unsigned)K * scale)), (unsigned)A.caps.hc);
-    const unsigned ps = min(next_pow2(max(64u, 8u * (unsigned)K * scale)), (unsigned)A.caps.phc);
+    // the shot is retried with larger ones
+    const unsigned hs = min(next_pow2(max(128u, 32u * (unsigned)K * scale)), (unsigned)A.caps.hc);
+    const unsigned ps = min(next_pow2(max(64u, 4u * (unsigned)K * scale)), (unsigned)A.caps.phc);
     C.hmask = hs - 1;
     C.pmask = ps - 1;
     clear_tables(S, C, lane);
@@ -1024,13 +1056,13 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
             S.ctr[C_WL] = k;
         }
         __syncwarp();
-        extend_many(S, C, __ldcg(&S.ctr[C_WL]), lane);
+        extend_many(S, C, ldr(&S.ctr[C_WL]), lane);
     }
     {
-        const int err = __ldcg(&S.ctr[C_ERR]);
+        const int err = ldr(&S.ctr[C_ERR]);
         if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
     }
-    const int npairs = __ldcg(&S.ctr[C_NPAIRS]);
+    const int npairs = ldr(&S.ctr[C_NPAIRS]);
     // connected components of pairs within b_1: min-label propagation
     for (int s = lane; s < K; s += WS) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
     __syncwarp();
@@ -1038,10 +1070,10 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
         bool changed = false;
         for (int i = lane; i < npairs; i += WS) {
             const int sl = S.plist[i];
-            if (__ldcg(&S.pval[sl]) > g.b1) continue;
-            const unsigned long long k = __ldcg(&S.pkey[sl]);
+            if (ldr(&S.pval[sl]) > g.b1) continue;
+            const unsigned long long k = ldr(&S.pkey[sl]);
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
-            const int la = __ldcg(&S.comp[a]), lb = __ldcg(&S.comp[b]);
+            const int la = ldr(&S.comp[a]), lb = ldr(&S.comp[b]);
             if (la != lb) {
                 const int m = min(la, lb);
                 atomicMin(&S.comp[a], m);
@@ -1061,8 +1093,8 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     __syncwarp();
     for (int i = lane; i < npairs; i += WS) {
         const int sl = S.plist[i];
-        if (__ldcg(&S.pval[sl]) > g.d1) continue;
-        const unsigned long long k = __ldcg(&S.pkey[sl]);
+        if (ldr(&S.pval[sl]) > g.d1) continue;
+        const unsigned long long k = ldr(&S.pkey[sl]);
         const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
         if (S.comp[a] == S.comp[b]) atomicAdd(&S.cst2[S.comp[a]], 1);
     }
@@ -1134,7 +1166,7 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     long long wint = 0;
     unsigned long long ob = 0;
     trace(S, C, lane, nhi, wint, ob);
-    const int err = __ldcg(&S.ctr[C_ERR]);
+    const int err = ldr(&S.ctr[C_ERR]);
     if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
     w_out = wint / 2;
     o_out = ob;
@@ -1191,12 +1223,63 @@ __global__ void __launch_bounds__(128, QEC_MIN_BLOCKS) batch_kernel(const __grid
         if (lane == 0) item = atomicAdd(counter, 1ull);
         item = __shfl_sync(FULL, item, 0);
         if ((long long)item >= limit) break;
-        const long long shot = a.pass == 0 ? (long long)item : (long long)a.overflow[item];
+        const long long shot = a.pass == 0 ? (a.order ? (long long)a.order[item] : (long long)item)
+                                           : (long long)a.overflow[item];
         decode_shot(a, S, shot, lane, deadline);
     }
 }
 
+struct GraphOrder {
+    int g[QEC_MAX_GRAPHS_PER_BATCH];
+};
+
+__global__ void graph_count_kernel(const int *gid, long long n, int ng, int *gcnt) {
+    __shared__ int local[QEC_MAX_GRAPHS_PER_BATCH];
+    for (int i = threadIdx.x; i < QEC_MAX_GRAPHS_PER_BATCH; i += blockDim.x) local[i] = 0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int g = gid[i];
+        if (g < 0 || g >= ng) g = 0;
+        atomicAdd(&local[g], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ng; i += blockDim.x)
+        if (local[i]) atomicAdd(&gcnt[i], local[i]);
+}
+
+__global__ void graph_scan_kernel(int *gcnt, int ng, GraphOrder go) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int acc = 0;
+    for (int k = 0; k < ng; k++) {
+        const int g = go.g[k];
+        gcnt[32 + g] = acc;
+        acc += gcnt[g];
+    }
+}
+
+__global__ void graph_scatter_kernel(const int *gid, long long n, int ng, int *gcnt, int *order) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int g = gid[i];
+        if (g < 0 || g >= ng) g = 0;
+        const int pos = atomicAdd(&gcnt[32 + g], 1);
+        order[pos] = (int)i;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_graph_sort(const int *graph_of_shot, long long n, int ng, const int *gorder, int *gcnt,
+                              int *order, cudaStream_t s) {
+    GraphOrder go;
+    for (int k = 0; k < QEC_MAX_GRAPHS_PER_BATCH; k++) go.g[k] = k < ng ? gorder[k] : 0;
+    cudaError_t e = cudaMemsetAsync(gcnt, 0, 64 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+    graph_count_kernel<<<blocks, 256, 0, s>>>(graph_of_shot, n, ng, gcnt);
+    graph_scan_kernel<<<1, 32, 0, s>>>(gcnt, ng, go);
+    graph_scatter_kernel<<<blocks, 256, 0, s>>>(graph_of_shot, n, ng, gcnt, order);
+    return cudaGetLastError();
+}
 
 long long slab_bytes_for(const SlabCaps &c) {
     Slab S;

@@ -9,13 +9,13 @@
 
 namespace qec {
 
-// One CSR slot of a detector: neighbour detector (-1 = boundary), internal
-// weight (2w), merged edge id.  16-byte aligned so one vector load fetches it.
-struct __align__(16) Slot {
-    int nbr;
+// One CSR slot of a detector, 8 bytes (one vector load): `code` is the
+// neighbour detector, or -1 - (merged edge id) for the edge to a boundary
+// vertex; `w` is the internal weight (2w).  Merged ids of detector-detector
+// slots live in DGraph::seid (read only to trace internal observables).
+struct __align__(8) Slot {
+    int code;
     int w;
-    int eid;
-    int pad;
 };
 
 // Device view of one graph, passed to kernels by value.
@@ -30,6 +30,7 @@ struct DGraph {
     const Slot *slot;                 // [row[n]]
     const unsigned long long *eobs;   // [merged edges]
     const int2 *eend;                 // [merged edges]: (lower detector endpoint, internal weight)
+    const int *seid;                  // [row[n]]: merged edge id of every slot
 };
 
 // Capacities of one warp's slab (per-shot working set).
@@ -63,6 +64,7 @@ struct BatchArgs {
     int *overflow;               // shot ids that overflowed the main pass
     int pass;                    // 0: all shots, 1: shots listed in overflow
     long long single_shot;       // >= 0: decode only this shot (plain path)
+    const int *order;            // pass 0 work order (shot indices), or NULL for 0, 1, 2, ...
     long long watchdog_ns;       // > 0: shots still running this long after the launch stop (budget status)
 };
 
@@ -72,6 +74,11 @@ long long slab_bytes_for(const SlabCaps &c);
 SlabCaps caps_for_kcap(int kcap, int table_factor = 1);
 cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s);
+// Order the shots of a mixed batch by graph (graphs in the order given by
+// gorder[0 .. ng)), so that concurrently running warps share one graph; gcnt
+// holds 64 ints of scratch.
+cudaError_t launch_graph_sort(const int *graph_of_shot, long long n, int ng, const int *gorder, int *gcnt,
+                              int *order, cudaStream_t s);
 // Resident blocks per SM of the batch kernel at this block size.
 int occupancy_blocks(int block_threads);
 // Largest block the batch kernel accepts.
