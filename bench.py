@@ -64,7 +64,10 @@ def parse():
     ap.add_argument("--scaling", action="store_true",
                     help="scaling study: d in {25,31,41,51} x p in {.001,.003,.005}, us per round vs d")
     ap.add_argument("--scaling-shots", type=int, default=10000)
-    ap.add_argument("--scaling-check", type=int, default=0, help="windows per point checked against the oracle")
+    ap.add_argument("--event-study", action="store_true",
+                    help="parallel event count per round, hierarchical vs global, d = 9..49, p = 1e-3..1e-5")
+    ap.add_argument("--study-shots", type=int, default=1024)
+    ap.add_argument("--study-save", default="", help="directory for the first outputs and diagnostics of every point")
     ap.add_argument("--scaling-save", default="", help="directory for the first outputs of every point")
     return ap.parse_args()
 
@@ -276,17 +279,56 @@ def scaling_study(q, args, dev):
                 k = min(64, S)
                 np.savez(os.path.join(args.scaling_save, "d%d_p%g.npz" % (d, p)), weight=out[1].cpu().numpy()[:k],
                          obs=q.to_uint64(out[0])[:k], status=st[:k], seed=args.seed + d * 1000 + int(p * 1e4))
-            if args.scaling_check > 0:
-                sys.path.insert(0, os.path.join(ROOT, "tests"))
-                from oracle_pool import oracle_decode
-                k = min(args.scaling_check, S)
-                rw, ro, rs = oracle_decode([pg], np.zeros(k, np.int32), list(syn[:k]))
-                gw, go = out[1].cpu().numpy()[:k], q.to_uint64(out[0])[:k]
-                row["oracle_checked"] = k
-                row["oracle_mismatch"] = int(np.count_nonzero((rw != gw) | (ro != go) | (rs != st[:k])))
             rows.append(row)
             print(json.dumps(row), flush=True)
             del t, out
+    q.set_tuning(kcap=-1, blocks_per_sm=-1, warps_per_block=-1)
+    return rows
+
+
+def event_study(q, args, dev):
+    """Parallel event count per round (Methods, "Numerical evaluation"): E_ideal of
+    the hierarchical execution and the event count of global sparse blossom, both
+    from the GPU's per-shot diagnostics, for d = 9, 13, ..., 49 (d rounds) and
+    p in {1e-3, 1e-4, 1e-5}.  Hierarchical and global results must agree
+    (Theorem 1).  --study-save keeps the first 64 shots' outputs of every point
+    for an offline comparison."""
+    import torch
+    rows = []
+    for p in (0.001, 0.0001, 0.00001):
+        for d in range(9, 50, 4):
+            pg = rotated_surface_code(d, d, p)
+            seed = args.seed + 7 * d + int(round(-np.log10(p)))
+            syn, _ = sample_shots(pg, args.study_shots, seed)
+            pc = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)
+            g = q.Graph.from_phys(pg)
+            q.set_tuning(kcap=max(64, int(pc.max() * 1.1) + 8), blocks_per_sm=-1, warps_per_block=-1)
+            t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
+            res = {}
+            for mode in ("hier", "global"):
+                o, w, st, dg = q.decode_batch_ex([g], t, mode=mode)
+                torch.cuda.synchronize()
+                res[mode] = (w.cpu().numpy(), q.to_uint64(o), st.cpu().numpy(), dg.cpu().numpy())
+            hw, ho, hs, hd = res["hier"]
+            gw, go, gs, gd = res["global"]
+            R = float(d)
+            row = {"d": d, "rounds": d, "p": p, "shots": int(syn.shape[0]), "mean_defects": float(pc.mean()),
+                   "e_ideal_per_round": float(hd[:, 0].mean() / R), "e_global_per_round": float(gd[:, 0].mean() / R),
+                   "e_hier_total_per_round": float(hd[:, 2].mean() / R),
+                   "max_e_ideal": int(hd[:, 0].max()), "max_e_global": int(gd[:, 0].max()),
+                   "t_ideal_mean": float(hd[:, 1].mean()), "t_global_mean": float(gd[:, 1].mean()),
+                   "level1_fraction": float(hd[:, 4].sum() / max(1, hd[:, 7].sum())),
+                   "hier_vs_global_mismatch": int(np.count_nonzero((hw != gw) | (ho != go) | (hs != gs))),
+                   "nonzero_status": int(np.count_nonzero(hs) + np.count_nonzero(gs))}
+            if args.study_save:
+                os.makedirs(args.study_save, exist_ok=True)
+                k = min(64, syn.shape[0])
+                np.savez(os.path.join(args.study_save, "d%d_p%g.npz" % (d, p)), seed=seed,
+                         **{"%s_%s" % (m, f): v[:k] for m, r in res.items()
+                            for f, v in zip(("weight", "obs", "status", "diag"), r)})
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            del t
     q.set_tuning(kcap=-1, blocks_per_sm=-1, warps_per_block=-1)
     return rows
 
@@ -353,6 +395,9 @@ def main():
         q.set_tuning(kcap=args.kcap)
     if args.scaling:
         scaling_study(q, args, torch.device("cuda", local))
+        return
+    if args.event_study:
+        event_study(q, args, torch.device("cuda", local))
         return
 
     graphs, gid, offs, syn = workload(args, rank)

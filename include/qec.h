@@ -152,6 +152,51 @@ int qec_decode_batch(const qec_graph *const *graphs, int32_t num_graphs,
                      uint64_t *obs_out, int64_t *weight_out, int32_t *status_out,
                      qec_cuda_stream stream);
 
+/* Execution modes of qec_decode_batch_ex. */
+enum {
+    QEC_MODE_HIERARCHICAL = 0,   /* Alg. 1 level-1 clusters, then one top-level run (Alg. 2) */
+    QEC_MODE_GLOBAL = 1          /* one sparse-blossom run over every detection event */
+};
+
+/* Per-shot diagnostics of qec_decode_batch_ex, QEC_DIAG_FIELDS int32 per shot.
+ * An event is one step of the matcher: a collision of two regions (events
+ * (a)-(c), (e), (g) of SI S1), a region reaching the boundary (f) or an inner
+ * blossom imploding (d).  The parallel event count E_ideal and its stopping
+ * time follow Methods, "Numerical evaluation": with t1 / E1 the largest
+ * stopping time / event count of the level-1 clusters (0 without any), the
+ * top-level run with N events, E_top(t1) of them at times <= t1, gives
+ * E_ideal = max(E1, E_top(t1)) + N - E_top(t1) (E1 when no event is left after
+ * level 1), which is the paper's recursion when every event above level 1
+ * forms one processing cluster (true whenever b_2 is at least the graph's
+ * diameter, as for the rotated surface codes of the benchmarks).  In global
+ * mode E_ideal is the run's whole event count.  Times are in internal units
+ * (twice the integer weights).  Shots whose status is not QEC_SHOT_OK and
+ * shots without detection events get all zeros. */
+#define QEC_DIAG_FIELDS 8
+enum {
+    QEC_DIAG_E_IDEAL = 0,       /* parallel event count */
+    QEC_DIAG_T_IDEAL = 1,       /* its critical-path stopping time */
+    QEC_DIAG_EVENTS = 2,        /* events of all runs of the shot */
+    QEC_DIAG_L1_CLUSTERS = 3,   /* level-1 processing clusters */
+    QEC_DIAG_L1_DEFECTS = 4,    /* detection events resolved at level 1 */
+    QEC_DIAG_TOP_EVENTS = 5,    /* events of the top-level (or global) run */
+    QEC_DIAG_BANDS = 6,         /* flooder band extensions of the event loop (GPU work, not an event) */
+    QEC_DIAG_DEFECTS = 7        /* detection events of the shot */
+};
+
+/* qec_decode_batch with an execution mode and optional diagnostics.
+ * mode        QEC_MODE_HIERARCHICAL (what qec_decode_batch runs) or
+ *             QEC_MODE_GLOBAL; both return a minimum-weight embedded matching
+ *             (Theorem 1), and with the canonical event order the same one.
+ * diag_out    device [num_shots][QEC_DIAG_FIELDS] int32, or NULL.
+ * Other arguments, errors and the asynchronous behaviour are those of
+ * qec_decode_batch; QEC_EINVAL also for an unknown mode. */
+int qec_decode_batch_ex(const qec_graph *const *graphs, int32_t num_graphs,
+                        const int32_t *graph_of_shot, const int64_t *syn_offset_words,
+                        const uint32_t *syndromes, int64_t num_shots, int32_t mode,
+                        uint64_t *obs_out, int64_t *weight_out, int32_t *status_out,
+                        int32_t *diag_out, qec_cuda_stream stream);
+
 /* Same as qec_decode_batch for one shot per kernel launch: shot s is decoded
  * by its own launch of a one-warp grid (the plain per-shot GPU path). */
 int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_shots,

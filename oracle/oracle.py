@@ -29,6 +29,8 @@ class OResult(C.Structure):
         ("num_clusters", C.c_int),
         ("level1_events", C.c_int),
         ("stop_time", C.c_longlong),
+        ("e_ideal", C.c_longlong),
+        ("t_ideal", C.c_longlong),
     ]
 
     def as_dict(self):
@@ -125,6 +127,20 @@ class OracleGraph:
                     int(self.dk.shape[0]), _p(self.dk, C.c_longlong), _p(self.bk, C.c_longlong),
                     C.byref(r), corr.ctypes.data if corr is not None else None)
         return (r, corr) if correction else r
+
+    def diag(self, defects, mode: str = "hier"):
+        """Decode one shot and return its result with the parallel-event-count
+        diagnostics (Methods, "Numerical evaluation") as a dict."""
+        r = self.decode(defects, mode)
+        out = {"weight": r.weight, "obs": r.obs, "status": r.status, "e_ideal": r.e_ideal,
+               "t_ideal": r.t_ideal, "events": r.events_implode + r.events_collide + r.events_boundary,
+               "l1_clusters": 0, "l1_defects": 0, "clusters_above_l1": 0, "defects": len(defects)}
+        if mode != "global" and len(defects):
+            _, lev, cl = self.cluster(defects)
+            out["l1_clusters"] = len(set(cl[lev == 1].tolist()))
+            out["l1_defects"] = int(np.count_nonzero(lev == 1))
+            out["clusters_above_l1"] = len(set(cl[lev > 1].tolist()))
+        return out
 
     def decode_bitmaps(self, syn: np.ndarray, mode: str = "hier"):
         L = lib()

@@ -32,6 +32,12 @@
  *     rule of Algorithm 2, simulated sequentially like the paper's simulator
  *     (Methods, "Numerical evaluation"): each cluster runs from t = 0 with every
  *     retained lower-level configuration present as frozen regions.
+ *  6. Parallel event count E_ideal (Methods, "Numerical evaluation"): per
+ *     cluster, its stopping time and the times of its events; the critical
+ *     path through the levels combines them level by level (the recursion is
+ *     written out where the levels run).  An event is one step of the loop of
+ *     item 3 (an implosion, a collision or a boundary contact); global mode
+ *     reports its whole event count.
  *
  * Checks computed for the tests: primal objective == dual objective (sum of all
  * duals equals the matched weight in internal units), dual feasibility of every
@@ -287,6 +293,8 @@ typedef struct {
     int *config;                  /* retained-configuration id of each node */
     int *touched;
     long long events[3];
+    long long *evt;               /* time of every applied event, in order */
+    long long nev, evcap;
     long long budget;
     int status;
 } Matcher;
@@ -328,6 +336,15 @@ static void m_free(Matcher *M) {
     free(M->present); free(M->y); free(M->alive); free(M->bpar); free(M->label);
     free(M->tpar); free(M->tps); free(M->tpo); free(M->mate); free(M->ms); free(M->mo);
     free(M->clen); free(M->cnode); free(M->cs); free(M->co); free(M->config); free(M->touched);
+    free(M->evt);
+}
+
+static void m_log_event(Matcher *M, long long t) {
+    if (M->nev == M->evcap) {
+        M->evcap = M->evcap ? 2 * M->evcap : 64;
+        M->evt = (long long *)realloc(M->evt, sizeof(long long) * (size_t)M->evcap);
+    }
+    M->evt[M->nev++] = t;
 }
 
 /* A leaf joins the run as a fresh root: radius 0, growing. */
@@ -626,6 +643,7 @@ static int m_run(Matcher *M) {
             if (M->alive[v] && M->bpar[v] < 0) M->y[v] += (long long)M->label[v] * dt;
         M->t = best.t;
         M->events[best.kind]++;
+        m_log_event(M, best.t);
         int st = ST_OK;
         if (best.kind == K_IMPLODE) {
             int B = m_top(M, best.lo);
@@ -685,6 +703,8 @@ typedef struct {
     int num_clusters;
     int level1_events;         /* detection events resolved at level 1 */
     long long stop_time;       /* largest stop time of any run */
+    long long e_ideal;         /* parallel event count (Methods, "Numerical evaluation") */
+    long long t_ideal;         /* its critical-path stopping time, internal units */
 } OResult;
 
 /* Mark the edges of the canonical path from detector src to detector x
@@ -865,6 +885,8 @@ int or_decode(const OGraph *g, int k, const int *det, int mode, int nlev,
         M.t = 0;
         st = m_run(&M);
         res->stop_time = M.t;
+        res->e_ideal = M.nev;     /* one run: every event is on the critical path */
+        res->t_ideal = M.t;
     } else {
         int *level = (int *)malloc(sizeof(int) * (size_t)k);
         int *cl = (int *)malloc(sizeof(int) * (size_t)k);
@@ -878,7 +900,17 @@ int or_decode(const OGraph *g, int k, const int *det, int mode, int nlev,
         }
         res->num_levels = maxlev;
         int *cfg_level = (int *)calloc((size_t)ncl + 1, sizeof(int));
+        /* Parallel event count (Methods, "Numerical evaluation"): t_lt and E_lt
+         * are the critical-path stopping time and event count through the
+         * levels below lv (both 0 below level 1).  A level-lv cluster C with
+         * stopping time s(C) and event history E_C(t) (events at times <= t)
+         * has t(C) = max(t_lt, s(C)) and
+         *     E(C) = max(E_lt, E_C(t_lt)) + E_C(t(C)) - E_C(t_lt);
+         * after the level, t_lt and E_lt become the maxima over its clusters
+         * (unchanged if the level has none). */
+        long long t_lt = 0, e_lt = 0;
         for (int lv = 1; st == ST_OK && lv <= maxlev; lv++) {
+            long long t_next = t_lt, e_next = e_lt;
             for (int c = 0; st == ST_OK && c < ncl; c++) {
                 int first = -1;
                 for (int a = 0; a < k; a++)
@@ -889,8 +921,20 @@ int or_decode(const OGraph *g, int k, const int *det, int mode, int nlev,
                 for (int a = 0; a < k; a++)
                     if (cl[a] == c) { m_add_root(&M, a); M.config[a] = c; }
                 M.t = 0;
+                const long long ev0 = M.nev;
                 st = m_run(&M);
                 if (M.t > res->stop_time) res->stop_time = M.t;
+                {
+                    const long long s_c = M.t;                  /* time of the cluster's last event */
+                    const long long n_c = M.nev - ev0;          /* E_C(t) for t >= s(C) */
+                    long long n_below = 0;                      /* E_C(t_lt) */
+                    for (long long i = ev0; i < M.nev; i++)
+                        if (M.evt[i] <= t_lt) n_below++;
+                    const long long t_c = s_c > t_lt ? s_c : t_lt;
+                    const long long e_c = (e_lt > n_below ? e_lt : n_below) + n_c - n_below;
+                    if (t_c > t_next) t_next = t_c;
+                    if (e_c > e_next) e_next = e_c;
+                }
                 /* touched retained configurations join cluster c's configuration */
                 int *hit = (int *)calloc((size_t)ncl + 1, sizeof(int));
                 for (int v = 0; v < M.nnodes; v++)
@@ -905,7 +949,11 @@ int or_decode(const OGraph *g, int k, const int *det, int mode, int nlev,
                     if (M.alive[v] && M.touched[v] && M.config[v] < 0) M.config[v] = c;
                 free(hit);
             }
+            t_lt = t_next;
+            e_lt = e_next;
         }
+        res->e_ideal = e_lt;
+        res->t_ideal = t_lt;
         free(cfg_level); free(level); free(cl);
     }
     if (st == ST_OK) m_finish(&M, res, g, corr);

@@ -76,6 +76,7 @@ def lib():
     L.qec_graph_get_info.argtypes = [vp, P(qec_graph_info)]
     L.qec_graph_merged_edges.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_uint64)]
     L.qec_decode_batch.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+    L.qec_decode_batch_ex.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, C.c_int32, vp, vp, vp, vp, vp]
     L.qec_decode_plain.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
     L.qec_decode_batch_static.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.qec_stream_create.argtypes = [C.c_size_t, C.c_int32, P(vp)]
@@ -222,6 +223,35 @@ def decode_batch(graphs, syndromes, graph_of_shot=None, syn_offset_words=None, n
                                   _dptr(syndromes), int(num_shots), _dptr(obs), _dptr(w), _dptr(st),
                                   _stream_handle(stream)))
     return obs, w, st
+
+
+MODES = {"hier": 0, "global": 1}
+DIAG_FIELDS = ("e_ideal", "t_ideal", "events", "l1_clusters", "l1_defects", "top_events", "bands", "defects")
+
+
+def decode_batch_ex(graphs, syndromes, graph_of_shot=None, syn_offset_words=None, num_shots=None,
+                    mode="hier", diag=True, out=None, stream=None):
+    """qec_decode_batch_ex: decode_batch with an execution mode ("hier" or
+    "global") and per-shot diagnostics.  Returns (obs, weight, status, diag)
+    with diag an int32 CUDA tensor [S, 8] (columns DIAG_FIELDS) or None."""
+    import torch
+    if isinstance(graphs, Graph):
+        graphs = [graphs]
+    if num_shots is None:
+        num_shots = int(graph_of_shot.shape[0]) if graph_of_shot is not None else \
+            int(syndromes.numel() // graphs[0].words)
+    dev = syndromes.device
+    if out is None:
+        out = (torch.empty(num_shots, dtype=torch.int64, device=dev),
+               torch.empty(num_shots, dtype=torch.int64, device=dev),
+               torch.empty(num_shots, dtype=torch.int32, device=dev))
+    obs, w, st = out
+    dg = torch.empty((num_shots, len(DIAG_FIELDS)), dtype=torch.int32, device=dev) if diag else None
+    arr = (C.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    _check(lib().qec_decode_batch_ex(arr, len(graphs), _dptr(graph_of_shot), _dptr(syn_offset_words),
+                                     _dptr(syndromes), int(num_shots), MODES[mode], _dptr(obs), _dptr(w),
+                                     _dptr(st), _dptr(dg), _stream_handle(stream)))
+    return obs, w, st, dg
 
 
 def decode_batch_static(graphs, syndromes, graph_of_shot=None, syn_offset_words=None, num_shots=None,

@@ -5,6 +5,7 @@
 // plain launch paths.  Kernels live in decoder.cu.
 
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -442,6 +443,11 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
     d.d1 = (int)std::min<long long>(g->dk[0], INT32_MAX / 4);
     d.b1 = (int)std::min<long long>(g->bk[0], INT32_MAX / 4);
     d.internal_obs = g->internal_obs;
+    {
+        long long wmin = LLONG_MAX;
+        for (int e = 0; e < g->m; e++) wmin = std::min<long long>(wmin, g->ew[e]);
+        d.hop2 = (g->m > 0 && 3 * wmin > (long long)d.b1) ? 1 : 0;
+    }
     d.row = g->d_row;
     d.slot = g->d_slot;
     d.eobs = g->d_eobs;
@@ -524,8 +530,9 @@ int qec_release_workspace(void) {
 static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, const int32_t *graph_of_shot,
                          const int64_t *syn_offset_words, const uint32_t *syndromes, int64_t num_shots,
                          uint64_t *obs_out, int64_t *weight_out, int32_t *status_out, qec_cuda_stream stream,
-                         bool plain) {
+                         bool plain, int32_t mode = QEC_MODE_HIERARCHICAL, int32_t *diag_out = nullptr) {
     if (num_shots < 0) return fail(QEC_EINVAL, "num_shots < 0");
+    if (mode != QEC_MODE_HIERARCHICAL && mode != QEC_MODE_GLOBAL) return fail(QEC_EINVAL, "unknown mode");
     if (num_shots == 0) return QEC_OK;
     if (!graphs || num_graphs < 1 || num_graphs > QEC_MAX_GRAPHS_PER_BATCH)
         return fail(QEC_EINVAL, "num_graphs out of range");
@@ -582,6 +589,8 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     a.queue = w.queue;
     a.overflow = w.overflow;
     a.watchdog_ns = 60LL * 1000 * 1000 * 1000;
+    a.mode = mode;
+    a.diag_out = diag_out;
     if (plain) {
         a.slabs = w.slabs;
         a.slab_bytes = w.slab_bytes;
@@ -630,6 +639,14 @@ int qec_decode_batch(const qec_graph *const *graphs, int32_t num_graphs, const i
                      uint64_t *obs_out, int64_t *weight_out, int32_t *status_out, qec_cuda_stream stream) {
     return decode_common(graphs, num_graphs, graph_of_shot, syn_offset_words, syndromes, num_shots, obs_out,
                          weight_out, status_out, stream, false);
+}
+
+int qec_decode_batch_ex(const qec_graph *const *graphs, int32_t num_graphs, const int32_t *graph_of_shot,
+                        const int64_t *syn_offset_words, const uint32_t *syndromes, int64_t num_shots, int32_t mode,
+                        uint64_t *obs_out, int64_t *weight_out, int32_t *status_out, int32_t *diag_out,
+                        qec_cuda_stream stream) {
+    return decode_common(graphs, num_graphs, graph_of_shot, syn_offset_words, syndromes, num_shots, obs_out,
+                         weight_out, status_out, stream, false, mode, diag_out);
 }
 
 int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_shots, uint64_t *obs_out,

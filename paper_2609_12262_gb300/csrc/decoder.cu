@@ -186,6 +186,10 @@ struct Shot {
     long long t;
     long long events;
     long long max_events;
+    // parallel-event-count bookkeeping of the current run (Methods, "Numerical
+    // evaluation"): matcher events applied, those at times <= tcut, the time of
+    // the last one, and flooder band extensions
+    int nm, ncut, tcut, tlast, nx;
 };
 
 __device__ __forceinline__ unsigned hslot(int v, unsigned mask) {
@@ -726,6 +730,13 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
                 if (S.inplay[s]) S.srad[s] += S.label[S.stop[s]] * dt;
         }
         C.t = tn;
+        if (kind == EV_EXTEND) {
+            C.nx++;
+        } else {
+            C.nm++;
+            if (tn <= C.tcut) C.ncut++;
+            C.tlast = (int)tn;
+        }
         __syncwarp();
         if (kind == EV_EXTEND) {
             // every growing region that reached its explored radius now
@@ -991,11 +1002,54 @@ __device__ int local_ball(const Slab &S, const Shot &C, int s, int Rb) {
     return settled;
 }
 
+// Level-1 neighbourhood of event s by enumeration, for graphs in which a path
+// of length <= Rb has at most two edges (DGraph::hop2): every event reached by
+// a path of one or two edges of length <= Rb is recorded through pair_upsert
+// (the minimum over those paths is the exact distance, since the shortest
+// path has at most two edges), and the boundary candidates through s itself or
+// a neighbour within Rb.  Same records as local_ball's for every use: pairs
+// within Rb exactly, and the canonical boundary contact whenever it lies within
+// Rb / 2 (a longer contact is only an upper bound, refined by the flooder
+// before a region can reach it).
+__device__ void local_2hop(const Slab &S, const Shot &C, int s, int Rb) {
+    const DGraph &g = C.g;
+    const int src = S.svtx[s];
+    unsigned long long bbest = EMPTY64;
+    const int r0 = __ldg(g.row + src), r1 = __ldg(g.row + src + 1);
+    for (int j = r0; j < r1; j++) {
+        const SlotV a = load_slot(g, j);
+        if (a.nbr < 0) {
+            const unsigned long long c = ((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.eid;
+            bbest = c < bbest ? c : bbest;
+            continue;
+        }
+        if (a.w > Rb) continue;
+        if (is_defect(C, a.nbr)) {
+            const int f = rank_of(S, C, a.nbr);
+            if (f > s) pair_upsert(S, C, s, f, a.w);
+        }
+        const int q0 = __ldg(g.row + a.nbr), q1 = __ldg(g.row + a.nbr + 1);
+        for (int k = q0; k < q1; k++) {
+            const SlotV b = load_slot(g, k);
+            const int nd = a.w + b.w;
+            if (b.nbr < 0) {
+                const unsigned long long c = ((unsigned long long)(unsigned)nd << 32) | (unsigned)b.eid;
+                bbest = c < bbest ? c : bbest;
+                continue;
+            }
+            if (nd > Rb || b.nbr == src || !is_defect(C, b.nbr)) continue;
+            const int f = rank_of(S, C, b.nbr);
+            if (f > s) pair_upsert(S, C, s, f, nd);
+        }
+    }
+    atomicMin(&S.sbnd[s], bbest);
+}
+
 // Decode one shot with hash tables scaled by `scale`; returns QEC_SHOT_* or -1
 // when the working set overflowed (retry with a larger scale).
 __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
                               int lane, unsigned scale, unsigned long long deadline, long long &w_out,
-                              unsigned long long &o_out) {
+                              unsigned long long &o_out, int *dg) {
     Shot C;
     C.g = g;
     C.ec = A.caps.ec; C.wc = A.caps.wc; C.cc = A.caps.cc;
@@ -1005,12 +1059,17 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     C.deadline = deadline;
     C.row = row;
     C.L = max(g.wmax, (g.b1 + 1) / 2) + 1;
+    C.nm = 0; C.ncut = 0; C.tcut = 0; C.tlast = 0; C.nx = 0;
     if (g.words > A.caps.wcap) return -2;
     const int K = load_defects(S, g, row, A.caps.kc, A.caps.wcap, lane);
     if (K < 0) return -2;
     C.K = K;
     C.max_events = min(A.max_events, 256LL * K + 4096);
-    if (K == 0) { w_out = 0; o_out = 0; return QEC_SHOT_OK; }
+    if (K == 0) {
+        w_out = 0; o_out = 0;
+        if (dg && lane < QEC_DIAG_FIELDS) dg[lane] = 0;   // no detection event: E_ideal = 0
+        return QEC_SHOT_OK;
+    }
     if (K > ID_MAX - 1 || 2 * K + 8 > A.caps.nc) return -2;
     C.nc = min(A.caps.nc, 2 * K + 16);   // leaves + at most K blossoms alive at once
     // about 8 (rarely ~15) explored entries and 1 (at most ~2) pair per
@@ -1037,124 +1096,143 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     }
     if (lane == 0) { S.ctr[C_ECOUNT] = 0; S.ctr[C_NFREE] = nfree; }
     __syncwarp();
-    // ---- Algorithm 1, level 1: every event's neighbourhood within b_1 by a
-    // lane-local Dijkstra (each lane its own events): pairs within b_1 with their
-    // exact distance (found by reaching the other event's vertex) and the
-    // canonical boundary candidate.  Events whose neighbourhood is too large for
-    // the lane go through the warp-wide flooder instead.
-    bool any_big = false;
-    for (int s = lane; s < K; s += WS) {
-        const int r = local_ball(S, C, s, g.b1);
-        if (r < 0) { S.cst0[s] = 1; any_big = true; } else S.cst0[s] = 0;
-    }
-    __syncwarp();
-    if (__any_sync(FULL, any_big)) {
-        if (lane == 0) {
-            int k = 0;
-            for (int s = 0; s < K; s++)
-                if (S.cst0[s]) { S.xsrc[k] = s; S.xR[k] = max(g.b1, C.band); k++; }
-            S.ctr[C_WL] = k;
+    // level-1 critical path (stopping time, event count), clusters, events
+    // resolved at level 1, events of all level-1 runs
+    int t1 = 0, e1 = 0, ncl1 = 0, nres1 = 0, ntot = 0;
+    if (A.mode == QEC_MODE_HIERARCHICAL) {
+        // ---- Algorithm 1, level 1: every event's neighbourhood within b_1 by a
+        // lane-local Dijkstra (each lane its own events): pairs within b_1 with their
+        // exact distance (found by reaching the other event's vertex) and the
+        // canonical boundary candidate.  Events whose neighbourhood is too large for
+        // the lane go through the warp-wide flooder instead.
+        bool any_big = false;
+        for (int s = lane; s < K; s += WS) {
+            int r = 0;
+        if (g.hop2) local_2hop(S, C, s, g.b1);
+        else r = local_ball(S, C, s, g.b1);
+            if (r < 0) { S.cst0[s] = 1; any_big = true; } else S.cst0[s] = 0;
         }
         __syncwarp();
-        extend_many(S, C, ldr(&S.ctr[C_WL]), lane);
-    }
-    {
-        const int err = ldr(&S.ctr[C_ERR]);
-        if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
-    }
-    const int npairs = ldr(&S.ctr[C_NPAIRS]);
-    // connected components of pairs within b_1: min-label propagation
-    for (int s = lane; s < K; s += WS) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
-    __syncwarp();
-    for (int round = 0; round <= K; round++) {
-        bool changed = false;
+        if (__any_sync(FULL, any_big)) {
+            if (lane == 0) {
+                int k = 0;
+                for (int s = 0; s < K; s++)
+                    if (S.cst0[s]) { S.xsrc[k] = s; S.xR[k] = max(g.b1, C.band); k++; }
+                S.ctr[C_WL] = k;
+            }
+            __syncwarp();
+            extend_many(S, C, ldr(&S.ctr[C_WL]), lane);
+        }
+        {
+            const int err = ldr(&S.ctr[C_ERR]);
+            if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
+        }
+        const int npairs = ldr(&S.ctr[C_NPAIRS]);
+        // connected components of pairs within b_1: min-label propagation
+        for (int s = lane; s < K; s += WS) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
+        __syncwarp();
+        for (int round = 0; round <= K; round++) {
+            bool changed = false;
+            for (int i = lane; i < npairs; i += WS) {
+                const int sl = S.plist[i];
+                if (ldr(&S.pval[sl]) > g.b1) continue;
+                const unsigned long long k = ldr(&S.pkey[sl]);
+                const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
+                const int la = ldr(&S.comp[a]), lb = ldr(&S.comp[b]);
+                if (la != lb) {
+                    const int m = min(la, lb);
+                    atomicMin(&S.comp[a], m);
+                    atomicMin(&S.comp[b], m);
+                    changed = true;
+                }
+            }
+            __syncwarp();
+            if (!__any_sync(FULL, changed)) break;
+        }
+        for (int s = lane; s < K; s += WS) {
+            const int r = S.comp[s];
+            atomicAdd(&S.cst0[r], 1);
+            const unsigned long long bb = S.sbnd[s];
+            if (bb != EMPTY64 && 2LL * (long long)(bb >> 32) <= (long long)g.b1) atomicOr(&S.cst1[r], 1);
+        }
+        __syncwarp();
         for (int i = lane; i < npairs; i += WS) {
             const int sl = S.plist[i];
-            if (ldr(&S.pval[sl]) > g.b1) continue;
+            if (ldr(&S.pval[sl]) > g.d1) continue;
             const unsigned long long k = ldr(&S.pkey[sl]);
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
-            const int la = ldr(&S.comp[a]), lb = ldr(&S.comp[b]);
-            if (la != lb) {
-                const int m = min(la, lb);
-                atomicMin(&S.comp[a], m);
-                atomicMin(&S.comp[b], m);
-                changed = true;
+            if (S.comp[a] == S.comp[b]) atomicAdd(&S.cst2[S.comp[a]], 1);
+        }
+        __syncwarp();
+        // ---- level-1 clusters: closed forms for isolated pairs / boundary singletons
+        bool need_general = false;
+        for (int s = lane; s < K; s += WS) {
+            const int r = S.comp[s];
+            const int size = S.cst0[r];
+            const bool ok = (long long)S.cst2[r] == (long long)size * (size - 1) / 2 &&
+                            ((S.cst1[r] & 1) || size % 2 == 0);
+            if (!ok) continue;
+            if (size == 1) {
+                const int bd = (int)(S.sbnd[s] >> 32);
+                S.alive[s] = 1; S.y[s] = bd; S.srad[s] = bd; S.label[s] = 0; S.bpar[s] = -1;
+                S.mate[s] = MATE_BOUNDARY; S.ms[s] = s; S.mo[s] = -1; S.stop[s] = s; S.nroot[s] = -1;
+                t1 = max(t1, bd); ncl1++; nres1++;   // one boundary event at time bd
+            } else if (size == 2) {
+                // partner: the other member
+                int other = -1;
+                for (int t2 = 0; t2 < K; t2++)
+                    if (t2 != s && S.comp[t2] == r) { other = t2; break; }
+                const int d = pair_get(S, C, s, other);
+                const long long ba = (long long)(S.sbnd[s] >> 32), bo = (long long)(S.sbnd[other] >> 32);
+                if (d / 2 <= ba && d / 2 <= bo) {
+                    S.alive[s] = 1; S.y[s] = d / 2; S.srad[s] = d / 2; S.label[s] = 0; S.bpar[s] = -1;
+                    S.mate[s] = other; S.ms[s] = s; S.mo[s] = other; S.stop[s] = s; S.nroot[s] = -1;
+                    t1 = max(t1, d / 2); nres1++;   // one collision at time d/2
+                    if (s < other) ncl1++;
+                } else {
+                    need_general = true;
+                    atomicOr(&S.cst1[r], 2);   // solve with the event loop
+                }
+            } else {
+                need_general = true;
+                atomicOr(&S.cst1[r], 2);
             }
         }
         __syncwarp();
-        if (!__any_sync(FULL, changed)) break;
-    }
-    for (int s = lane; s < K; s += WS) {
-        const int r = S.comp[s];
-        atomicAdd(&S.cst0[r], 1);
-        const unsigned long long bb = S.sbnd[s];
-        if (bb != EMPTY64 && 2LL * (long long)(bb >> 32) <= (long long)g.b1) atomicOr(&S.cst1[r], 1);
-    }
-    __syncwarp();
-    for (int i = lane; i < npairs; i += WS) {
-        const int sl = S.plist[i];
-        if (ldr(&S.pval[sl]) > g.d1) continue;
-        const unsigned long long k = ldr(&S.pkey[sl]);
-        const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
-        if (S.comp[a] == S.comp[b]) atomicAdd(&S.cst2[S.comp[a]], 1);
-    }
-    __syncwarp();
-    // ---- level-1 clusters: closed forms for isolated pairs / boundary singletons
-    bool need_general = false;
-    for (int s = lane; s < K; s += WS) {
-        const int r = S.comp[s];
-        const int size = S.cst0[r];
-        const bool ok = (long long)S.cst2[r] == (long long)size * (size - 1) / 2 &&
-                        ((S.cst1[r] & 1) || size % 2 == 0);
-        if (!ok) continue;
-        if (size == 1) {
-            const int bd = (int)(S.sbnd[s] >> 32);
-            S.alive[s] = 1; S.y[s] = bd; S.srad[s] = bd; S.label[s] = 0; S.bpar[s] = -1;
-            S.mate[s] = MATE_BOUNDARY; S.ms[s] = s; S.mo[s] = -1; S.stop[s] = s; S.nroot[s] = -1;
-        } else if (size == 2) {
-            // partner: the other member
-            int other = -1;
-            for (int t2 = 0; t2 < K; t2++)
-                if (t2 != s && S.comp[t2] == r) { other = t2; break; }
-            const int d = pair_get(S, C, s, other);
-            const long long ba = (long long)(S.sbnd[s] >> 32), bo = (long long)(S.sbnd[other] >> 32);
-            if (d / 2 <= ba && d / 2 <= bo) {
-                S.alive[s] = 1; S.y[s] = d / 2; S.srad[s] = d / 2; S.label[s] = 0; S.bpar[s] = -1;
-                S.mate[s] = other; S.ms[s] = s; S.mo[s] = other; S.stop[s] = s; S.nroot[s] = -1;
-            } else {
-                need_general = true;
-                atomicOr(&S.cst1[r], 2);   // solve with the event loop
+        t1 = (int)__reduce_max_sync(FULL, (unsigned)t1);
+        ncl1 = (int)__reduce_add_sync(FULL, (unsigned)ncl1);
+        nres1 = (int)__reduce_add_sync(FULL, (unsigned)nres1);
+        e1 = ncl1 > 0 ? 1 : 0;
+        ntot = ncl1;
+        need_general = __any_sync(FULL, need_general);
+        if (need_general) {
+            for (int r = 0; r < K; r++) {
+                if (S.comp[r] != r || !(S.cst1[r] & 2)) continue;
+                for (int s = lane; s < K; s += WS)
+                    if (S.comp[s] == r) make_root(S, s);
+                __syncwarp();
+                C.nm = 0; C.tlast = 0;
+                const int st = run_matcher(S, C, lane, nhi);
+                if (st != RUN_OK) {
+                    if (st == RUN_CAP) return -1;
+                    return st == RUN_NOSOL ? QEC_SHOT_NO_SOLUTION
+                           : st == RUN_BUDGET ? QEC_SHOT_BUDGET_EXCEEDED : QEC_SHOT_INTERNAL;
+                }
+                for (int s = lane; s < K; s += WS)
+                    if (S.comp[s] == r) S.inplay[s] = 0;
+                __syncwarp();
+                e1 = max(e1, C.nm); t1 = max(t1, C.tlast); ntot += C.nm; ncl1++; nres1 += S.cst0[r];
             }
-        } else {
-            need_general = true;
-            atomicOr(&S.cst1[r], 2);
-        }
-    }
-    __syncwarp();
-    need_general = __any_sync(FULL, need_general);
-    if (need_general) {
-        for (int r = 0; r < K; r++) {
-            if (S.comp[r] != r || !(S.cst1[r] & 2)) continue;
-            for (int s = lane; s < K; s += WS)
-                if (S.comp[s] == r) make_root(S, s);
-            __syncwarp();
-            const int st = run_matcher(S, C, lane, nhi);
-            if (st != RUN_OK) {
-                if (st == RUN_CAP) return -1;
-                return st == RUN_NOSOL ? QEC_SHOT_NO_SOLUTION
-                       : st == RUN_BUDGET ? QEC_SHOT_BUDGET_EXCEEDED : QEC_SHOT_INTERNAL;
-            }
-            for (int s = lane; s < K; s += WS)
-                if (S.comp[s] == r) S.inplay[s] = 0;
-            __syncwarp();
         }
     }
     // ---- top level: every remaining event from t = 0, level-1 states frozen
+    // (global mode: every event, from an empty state)
     for (int s = lane; s < K; s += WS) {
         if (S.alive[s] || S.stop[s] != s) S.inplay[s] = 1;   // stopped level-1 configuration
         else make_root(S, s);
     }
     __syncwarp();
+    C.nm = 0; C.ncut = 0; C.tlast = 0; C.tcut = t1;
     {
         const int st = run_matcher(S, C, lane, nhi);
         if (st != RUN_OK) {
@@ -1170,6 +1248,20 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
     w_out = wint / 2;
     o_out = ob;
+    if (dg && lane == 0) {
+        // parallel event count over level 1 and the top level (Methods,
+        // "Numerical evaluation"): the top run's events up to the level-1
+        // critical-path time t1 overlap level 1, the rest extend it
+        const int ntop = C.nm;
+        dg[QEC_DIAG_E_IDEAL] = ntop > 0 ? max(e1, C.ncut) + ntop - C.ncut : e1;
+        dg[QEC_DIAG_T_IDEAL] = ntop > 0 ? max(t1, C.tlast) : t1;
+        dg[QEC_DIAG_EVENTS] = ntot + ntop;
+        dg[QEC_DIAG_L1_CLUSTERS] = ncl1;
+        dg[QEC_DIAG_L1_DEFECTS] = nres1;
+        dg[QEC_DIAG_TOP_EVENTS] = ntop;
+        dg[QEC_DIAG_BANDS] = C.nx;
+        dg[QEC_DIAG_DEFECTS] = K;
+    }
     return QEC_SHOT_OK;
 }
 
@@ -1183,8 +1275,9 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, i
     int status = -1;
     long long w = 0;
     unsigned long long o = 0;
+    int *dg = A.diag_out ? A.diag_out + shot * QEC_DIAG_FIELDS : nullptr;
     for (unsigned scale = 1; scale <= 64 && status == -1; scale *= 4)
-        status = decode_attempt(A, S, g, row, lane, scale, deadline, w, o);
+        status = decode_attempt(A, S, g, row, lane, scale, deadline, w, o, dg);
     if (status < 0) {
         status = QEC_SHOT_CAPACITY;
         if (A.pass == 0 && A.single_shot < 0 && lane == 0) {
@@ -1194,6 +1287,7 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, i
         w = 0;
         o = 0;
     }
+    if (dg && status != QEC_SHOT_OK && lane < QEC_DIAG_FIELDS) dg[lane] = 0;
     if (lane == 0) {
         A.w_out[shot] = w;
         A.obs_out[shot] = o;

@@ -25,7 +25,8 @@ struct DGraph {
     int wmax;          // largest internal weight
     int d1, b1;        // Algorithm 3 level-1 diameter / buffer (internal units)
     int internal_obs;  // some detector-detector edge carries an observable
-    int pad0, pad1;
+    int hop2;          // 3 x smallest internal weight > b1: a path of length <= b1 has at most two edges
+    int pad1;
     const int *row;                   // [n + 1]
     const Slot *slot;                 // [row[n]]
     const unsigned long long *eobs;   // [merged edges]
@@ -66,6 +67,8 @@ struct BatchArgs {
     long long single_shot;       // >= 0: decode only this shot (plain path)
     const int *order;            // pass 0 work order (shot indices), or NULL for 0, 1, 2, ...
     long long watchdog_ns;       // > 0: shots still running this long after the launch stop (budget status)
+    int mode;                    // QEC_MODE_HIERARCHICAL or QEC_MODE_GLOBAL
+    int *diag_out;               // [num_shots][QEC_DIAG_FIELDS] per-shot counters, or NULL
 };
 
 long long slab_bytes_for(const SlabCaps &c);

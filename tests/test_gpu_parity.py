@@ -58,6 +58,9 @@ CASES = [
     ("d7_p04_blossoms", dict(d=7, p=0.04), 2000, 4),
     ("d11_p02", dict(d=11, p=0.02), 600, 5),
     ("d3_p10_dense", dict(d=3, p=0.10), 2000, 6),
+    # weights spread enough that level-1 neighbourhoods need the bounded search
+    ("d9_wide_nonuniform", dict(d=9, p_range=(0.001, 0.02), p_seed=3), 2000, 9),
+    ("d7_wider_nonuniform", dict(d=7, p_range=(0.0005, 0.05), p_seed=3), 2000, 10),
 ]
 
 
