@@ -116,12 +116,14 @@ struct Slab {
     // per detection event (source)
     int *svtx, *srad, *stop, *sR, *sbeg, *scnt, *sexh, *inplay, *comp, *cst0, *cst1, *cst2;
     unsigned long long *sbnd;
-    // explored entries: key (vertex << 32 | source), value exact distance
+    // explored entries: key (vertex << 32 | source), value exact distance;
+    // `ent` holds the table slots of every source's bands (band lists)
     unsigned long long *hkey;
     int *hval;
     int *ent;
-    unsigned long long *wl0, *wl1, *tl;   // (vertex << 32 | source) work lists / new entries
+    unsigned long long *wl0, *wl1, *tl;   // work lists (table slots) / new entries (slot << 32 | position)
     int *xsrc, *xR, *xcnt, *xcur;         // sources being extended, target radii, band counts
+    int *xidx;                            // position of a source in xsrc during an extension
     int *wcum;                            // detection events in syndrome words before word w
     // pairs: key (lo << 32 | hi), value distance, list of used slots
     unsigned long long *pkey;
@@ -153,6 +155,7 @@ __host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &
     S.wl0 = bump<unsigned long long>(p, c.wc); S.wl1 = bump<unsigned long long>(p, c.wc);
     S.tl = bump<unsigned long long>(p, c.ec);
     S.xsrc = bump<int>(p, c.kc); S.xR = bump<int>(p, c.kc); S.xcnt = bump<int>(p, c.kc); S.xcur = bump<int>(p, c.kc);
+    S.xidx = bump<int>(p, c.kc);
     S.wcum = bump<int>(p, c.wcap);
     S.pkey = bump<unsigned long long>(p, c.phc); S.pval = bump<int>(p, c.phc); S.plist = bump<int>(p, c.phc);
     S.y = bump<int>(p, c.nc); S.bpar = bump<int>(p, c.nc); S.label = bump<int>(p, c.nc);
@@ -215,8 +218,9 @@ __device__ int ht_get(const Slab &S, const Shot &C, int v, int s) {
     return INF32;
 }
 
-// insert-or-decrease; returns 1 inserted, 2 decreased, 0 unchanged, -1 table full
-__device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d) {
+// insert-or-decrease; returns 1 inserted, 2 decreased, 0 unchanged, -1 table
+// full; `slot` receives the entry's table slot
+__device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d, unsigned &slot) {
     const unsigned long long key = ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
     unsigned i = hslot(v, C.hmask);
     for (unsigned n = 0; n <= C.hmask; n++) {
@@ -225,12 +229,14 @@ __device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d) {
             unsigned long long prev = atomicCAS(&S.hkey[i], EMPTY64, key);
             if (prev == EMPTY64) {
                 atomicMin(&S.hval[i], d);
+                slot = i;
                 return 1;
             }
             k = prev;
         }
         if (k == key) {
             int old = atomicMin(&S.hval[i], d);
+            slot = i;
             return d < old ? 2 : 0;
         }
         i = (i + 1) & C.hmask;
@@ -330,66 +336,71 @@ __device__ __forceinline__ unsigned long long vs_pack(int v, int s) {
 
 // Grow the explored balls of the sources xsrc[0 .. nx) from radius sR[s] to
 // xR[i] (xR[i] - sR[s] >= largest weight), all at once: the previous band of
-// each source is the frontier, label-correcting relaxation runs on (vertex,
-// source) work lists until no distance changes, every new entry is checked
-// for contacts with the other sources' balls, and each source's new band is
-// stored contiguously in `ent` as its next frontier.  All lanes call.
+// each source is the frontier, label-correcting relaxation runs on work lists
+// of table slots (a slot's key names the vertex and source, its value the
+// current distance) until no distance changes, every new entry is checked for
+// contacts with the other sources' balls, and each source's new band is stored
+// contiguously in `ent` as its next frontier.  All lanes call.
 __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
     const DGraph &g = C.g;
     if (nx <= 0) return;
     __syncwarp();
     if (lane == 0) { S.ctr[C_TL] = 0; S.ctr[C_WL] = 0; }
-    for (int i = lane; i < nx; i += WS) S.xcnt[i] = 0;
+    for (int i = lane; i < nx; i += WS) { S.xcnt[i] = 0; S.xidx[S.xsrc[i]] = i; }
     __syncwarp();
+    unsigned *F = reinterpret_cast<unsigned *>(S.wl0), *Wn = reinterpret_cast<unsigned *>(S.wl1);
     // initial frontier: the previous band of every listed source; a source
     // never explored so far starts from its own vertex at distance 0
     for (int i = lane; i < nx; i += WS) {
         const int s = S.xsrc[i];
         if (S.sR[s] < 0) {
-            const int v = S.svtx[s];
-            if (ht_upsert(S, C, v, s, 0) == 1) {
+            unsigned hs;
+            const int r = ht_upsert(S, C, S.svtx[s], s, 0, hs);
+            if (r < 0) continue;
+            if (r == 1) {
                 const int e = atomicAdd(&S.ctr[C_TL], 1);
-                if (e < C.ec) S.tl[e] = vs_pack(v, i); else set_err(S, ERR_CAP);
+                if (e < C.ec) S.tl[e] = ((unsigned long long)hs << 32) | (unsigned)i; else set_err(S, ERR_CAP);
             }
             const int w = atomicAdd(&S.ctr[C_WL], 1);
-            if (w < C.wc) S.wl0[w] = vs_pack(v, i); else set_err(S, ERR_CAP);
+            if (w < C.wc) F[w] = hs; else set_err(S, ERR_CAP);
             continue;
         }
         const int fb = S.sbeg[s], fc = S.scnt[s];
         const int base = atomicAdd(&S.ctr[C_WL], fc);
         for (int k = 0; k < fc; k++) {
-            if (base + k < C.wc) S.wl0[base + k] = vs_pack(S.ent[fb + k], i);
+            if (base + k < C.wc) F[base + k] = (unsigned)S.ent[fb + k];
             else set_err(S, ERR_CAP);
         }
     }
     __syncwarp();
     int nf = min(ldr(&S.ctr[C_WL]), C.wc);
-    unsigned long long *F = S.wl0, *Wn = S.wl1;
     for (int iter = 0;; iter++) {
         if (iter >= 4096) { if (lane == 0) set_err(S, ERR_INTERNAL); break; }
         __syncwarp();
         if (lane == 0) S.ctr[C_WL] = 0;
         __syncwarp();
         for (int i = lane; i < nf; i += WS) {
-            const unsigned long long it = F[i];
-            const int x = (int)(it >> 32), xi = (int)(unsigned)(it & 0xffffffffu);
-            const int s = S.xsrc[xi];
+            const unsigned hx = F[i];
+            const unsigned long long key = ldr(&S.hkey[hx]);
+            const int x = (int)(key >> 32), s = (int)(unsigned)(key & 0xffffffffu);
+            const int dx = ldr(&S.hval[hx]);
+            const int xi = S.xidx[s];
             const int Rn = S.xR[xi];
-            const int dx = ht_get(S, C, x, s);
             const int r0 = __ldg(g.row + x), r1 = __ldg(g.row + x + 1);
             for (int j = r0; j < r1; j++) {
                 SlotV sl = load_slot(g, j);
                 const int nd = dx + sl.w;
                 if (sl.nbr < 0) { bnd_update(S, s, nd, sl.eid); continue; }
                 if (nd > Rn) continue;
-                int r = ht_upsert(S, C, sl.nbr, s, nd);
+                unsigned hs;
+                const int r = ht_upsert(S, C, sl.nbr, s, nd, hs);
                 if (r == 1) {
                     const int e = agg_inc(&S.ctr[C_TL], lane);
-                    if (e < C.ec) S.tl[e] = vs_pack(sl.nbr, xi); else set_err(S, ERR_CAP);
+                    if (e < C.ec) S.tl[e] = ((unsigned long long)hs << 32) | (unsigned)xi; else set_err(S, ERR_CAP);
                 }
                 if (r >= 1) {
                     const int w = agg_inc(&S.ctr[C_WL], lane);
-                    if (w < C.wc) Wn[w] = vs_pack(sl.nbr, xi); else set_err(S, ERR_CAP);
+                    if (w < C.wc) Wn[w] = hs; else set_err(S, ERR_CAP);
                 }
             }
         }
@@ -398,7 +409,7 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
         const int err = ldr(&S.ctr[C_ERR]);
         if (nw == 0 || err) break;
         nf = min(nw, C.wc);
-        unsigned long long *t = F; F = Wn; Wn = t;
+        unsigned *t = F; F = Wn; Wn = t;
     }
     __syncwarp();
     const int nt = min(ldr(&S.ctr[C_TL]), C.ec);
@@ -437,10 +448,10 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
     // between them, the first vertex at distance >= Rad(a) from a lies in b's
     // region and within Rad(a) + largest weight of a.
     for (int i = lane; i < nt; i += WS) {
-        const unsigned long long it = S.tl[i];
-        const int yv = (int)(it >> 32);
-        const int s = S.xsrc[(int)(unsigned)(it & 0xffffffffu)];
-        const int dy = ht_get(S, C, yv, s);
+        const unsigned hy = (unsigned)(S.tl[i] >> 32);
+        const unsigned long long key = ldr(&S.hkey[hy]);
+        const int yv = (int)(key >> 32), s = (int)(unsigned)(key & 0xffffffffu);
+        const int dy = ldr(&S.hval[hy]);
         contacts_at(S, C, s, yv, dy);
         if (yv != S.svtx[s] && is_defect(C, yv)) {
             const int f = rank_of(S, C, yv);
