@@ -34,6 +34,11 @@
 //
 // Every loop is bounded: the event budget, hash probe lengths and list
 // capacities end a shot with a status code instead of spinning.
+//
+// The rarely taken matcher steps (augment, blossom, shatter), the tracing and
+// the bounded level-1 search are kept out of line (__noinline__): the event
+// loop and the flooder stay inlined, and the kernel's hot code stays small
+// enough for the instruction cache.
 
 #include <algorithm>
 #include <climits>
@@ -379,24 +384,54 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
         __syncwarp();
         if (lane == 0) S.ctr[C_WL] = 0;
         __syncwarp();
-        for (int i = lane; i < nf; i += WS) {
-            const unsigned hx = F[i];
-            const unsigned long long key = ldr(&S.hkey[hx]);
-            const int x = (int)(key >> 32), s = (int)(unsigned)(key & 0xffffffffu);
-            const int dx = ldr(&S.hval[hx]);
-            const int xi = S.xidx[s];
-            const int Rn = S.xR[xi];
-            const int r0 = __ldg(g.row + x), r1 = __ldg(g.row + x + 1);
-            for (int j = r0; j < r1; j++) {
-                SlotV sl = load_slot(g, j);
-                const int nd = dx + sl.w;
+        // one lane per (work item, adjacency slot): items are taken 32 at a
+        // time, their slots numbered by a warp prefix sum of the degrees, and
+        // slot t goes to lane t mod 32 (its item found by binary search)
+        for (int base = 0; base < nf; base += WS) {
+            const int i = base + lane;
+            unsigned long long key = 0;
+            int dx = 0, Rn = -1, r0 = 0, deg = 0, xi = 0;
+            if (i < nf) {
+                const unsigned hx = F[i];
+                key = ldr(&S.hkey[hx]);
+                dx = ldr(&S.hval[hx]);
+                const int x = (int)(key >> 32);
+                xi = S.xidx[(int)(unsigned)(key & 0xffffffffu)];
+                Rn = S.xR[xi];
+                r0 = __ldg(g.row + x);
+                deg = __ldg(g.row + x + 1) - r0;
+            }
+            int incl = deg;
+            for (int o = 1; o < WS; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(FULL, incl, WS - 1);
+            const int excl = incl - deg;
+            for (int t0 = 0; t0 < total; t0 += WS) {
+                const int t = t0 + lane;
+                // owner: the last lane whose first slot number is <= t
+                int ow = 0;
+                for (int step = WS / 2; step > 0; step >>= 1) {
+                    const int e = __shfl_sync(FULL, excl, ow + step);
+                    if (e <= t) ow += step;
+                }
+                const unsigned long long okey = __shfl_sync(FULL, key, ow);
+                const int odx = __shfl_sync(FULL, dx, ow);
+                const int oRn = __shfl_sync(FULL, Rn, ow);
+                const int oj = __shfl_sync(FULL, r0 - excl, ow) + t;
+                const int oxi = __shfl_sync(FULL, xi, ow);
+                if (t >= total) continue;
+                const int s = (int)(unsigned)(okey & 0xffffffffu);
+                const SlotV sl = load_slot(g, oj);
+                const int nd = odx + sl.w;
                 if (sl.nbr < 0) { bnd_update(S, s, nd, sl.eid); continue; }
-                if (nd > Rn) continue;
+                if (nd > oRn) continue;
                 unsigned hs;
                 const int r = ht_upsert(S, C, sl.nbr, s, nd, hs);
                 if (r == 1) {
                     const int e = agg_inc(&S.ctr[C_TL], lane);
-                    if (e < C.ec) S.tl[e] = ((unsigned long long)hs << 32) | (unsigned)xi; else set_err(S, ERR_CAP);
+                    if (e < C.ec) S.tl[e] = ((unsigned long long)hs << 32) | (unsigned)oxi; else set_err(S, ERR_CAP);
                 }
                 if (r >= 1) {
                     const int w = agg_inc(&S.ctr[C_WL], lane);
@@ -491,7 +526,7 @@ __device__ void flip_to_root(const Slab &S, int A) {
 }
 
 // Events (b), (f), (g).  B < 0: boundary.  All lanes call.
-__device__ void ev_augment(const Slab &S, Shot &C, int A, int a, int B, int b, int lane, int nhi) {
+__device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, int B, int b, int lane, int nhi) {
     int rA = 0, rB = -3;
     if (lane == 0) {
         rA = S.nroot[A];
@@ -525,7 +560,7 @@ __device__ void ev_grow(const Slab &S, int A, int a, int B, int b) {
 }
 
 // Event (c): outer A, B in one tree form a blossom.  All lanes call.
-__device__ void ev_blossom(const Slab &S, Shot &C, int A, int a, int B, int b, int lane, int &nhi) {
+__device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, int B, int b, int lane, int &nhi) {
     int N = -1, L = -1, Lroot = 0;
     if (lane == 0) {
         int na = 0, nb = 0;
@@ -586,7 +621,7 @@ __device__ void ev_blossom(const Slab &S, Shot &C, int A, int a, int B, int b, i
 }
 
 // Event (d): inner blossom B with zero dual shatters.  All lanes call.
-__device__ void ev_shatter(const Slab &S, Shot &C, int B, int lane) {
+__device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, int lane) {
     for (int s = lane; s < C.K; s += WS)
         if (S.stop[s] == B) {
             const int c = child_of(S, B, s);
@@ -819,7 +854,7 @@ __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int
 
 // Expand the final matching into leaf-level pairs (tmpa[i], tmpb[i]; tmpb = -1
 // for a boundary match) and accumulate weight (internal units) and obs.
-__device__ void trace(const Slab &S, Shot &C, int lane, int nhi, long long &wint, unsigned long long &obs) {
+__device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, long long &wint, unsigned long long &obs) {
     int np = 0;
     if (lane == 0) {
         int *stk = S.stk;
@@ -965,7 +1000,7 @@ constexpr int LB_CAP = 64;   // vertices one lane holds while exploring one even
 // tables): records every other event within Rb through pair_upsert (from the
 // lower-ranked end only) and the canonical boundary candidate of s.  Returns
 // the number of vertices settled, or -1 if more than LB_CAP lie within Rb.
-__device__ int local_ball(const Slab &S, const Shot &C, int s, int Rb) {
+__device__ __noinline__ int local_ball(const Slab &S, const Shot &C, int s, int Rb) {
     const DGraph &g = C.g;
     int vv[LB_CAP], dd[LB_CAP];
     unsigned long long fin = 0;   // settled flags
