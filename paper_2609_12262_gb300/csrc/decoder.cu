@@ -68,7 +68,7 @@ enum { MATE_NONE = -1, MATE_BOUNDARY = -2 };
 
 // slab counters
 enum { C_ECOUNT = 0, C_WL = 1, C_NPAIRS = 2, C_CCOUNT = 3, C_NFREE = 4, C_ERR = 5, C_HFILL = 6, C_NHI = 7,
-       C_TL = 8, C_CHANGED = 9, C_TOTAL = 16 };
+       C_TL = 8, C_CHANGED = 9, C_TNP = 10, C_TNX = 11, C_TOTAL = 16 };
 enum { ERR_CAP = 1, ERR_INTERNAL = 2 };
 
 __device__ __forceinline__ unsigned long long ev_key(long long t, int kind, int lo, int hi) {
@@ -715,19 +715,19 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
         bool outer = false, bad = false;
         int inner_leaf_min = INT_MAX;
         for (int s = lane; s < C.K; s += WS) {
-            if (!S.inplay[s]) continue;
-            const int A = S.stop[s];
+            // independent loads first, one dependent load (the label) after
+            const int ip = S.inplay[s], A = S.stop[s], rad = S.srad[s], exh = S.sexh[s], sR = S.sR[s];
+            const unsigned long long bb = ldr(&S.sbnd[s]);
+            if (!ip) continue;
             const int lab = S.label[A];
             if (lab == 1) {
                 outer = true;
-                const int rad = S.srad[s];
-                if (!S.sexh[s]) {
+                if (!exh) {
                     // due when Rad(s) + L would pass the explored radius; a region that
                     // just started growing (or was never explored) is due at once
-                    const int ahead = S.sR[s] - C.L + 1 - rad;
+                    const int ahead = sR - C.L + 1 - rad;
                     best = min(best, ev_key(C.t + (ahead > 0 ? ahead : 0), EV_EXTEND, s, 0));
                 }
-                const unsigned long long bb = ldr(&S.sbnd[s]);
                 if (bb != EMPTY64) {
                     const int bd = (int)(bb >> 32);
                     if (bd < rad) bad = true;
@@ -742,12 +742,12 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
             const int sl = S.plist[i];
             const unsigned long long k = ldr(&S.pkey[sl]);
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
-            if (!S.inplay[a] || !S.inplay[b]) continue;
-            const int A = S.stop[a], B = S.stop[b];
-            if (A == B) continue;
+            const int ia = S.inplay[a], ib = S.inplay[b], A = S.stop[a], B = S.stop[b];
+            const int ra = S.srad[a], rb = S.srad[b], pv = ldr(&S.pval[sl]);
+            if (!ia || !ib || A == B) continue;
             const int r = S.label[A] + S.label[B];
             if (r <= 0) continue;
-            const int gap = ldr(&S.pval[sl]) - S.srad[a] - S.srad[b];
+            const int gap = pv - ra - rb;
             if (gap < 0 || gap % r) { bad = true; continue; }
             best = min(best, ev_key(C.t + gap / r, EV_COLLIDE, a, b));
         }
@@ -855,41 +855,49 @@ __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int
 // Expand the final matching into leaf-level pairs (tmpa[i], tmpb[i]; tmpb = -1
 // for a boundary match) and accumulate weight (internal units) and obs.
 __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, long long &wint, unsigned long long &obs) {
-    int np = 0;
+    // matched top-level nodes, lane-parallel: each match appends its leaf pair
+    // and queues the blossoms on either side for expansion (stack seeds)
+    if (lane == 0) { S.ctr[C_TNP] = 0; S.ctr[C_TNX] = 0; }
+    __syncwarp();
+    int *stk = S.stk;
+    for (int v = lane; v < nhi; v += WS) {
+        if (!S.alive[v] || S.bpar[v] >= 0) continue;
+        const int mt = S.mate[v];
+        if (mt == MATE_BOUNDARY) {
+            const int k = agg_inc(&S.ctr[C_TNP], lane);
+            S.tmpa[k] = S.ms[v]; S.tmpb[k] = -1;
+            if (v >= C.K) { const int x = atomicAdd(&S.ctr[C_TNX], 1); stk[2 * x] = v; stk[2 * x + 1] = S.ms[v]; }
+        } else if (mt >= 0 && v < mt) {
+            const int k = agg_inc(&S.ctr[C_TNP], lane);
+            S.tmpa[k] = S.ms[v]; S.tmpb[k] = S.mo[v];
+            if (v >= C.K) { const int x = atomicAdd(&S.ctr[C_TNX], 1); stk[2 * x] = v; stk[2 * x + 1] = S.ms[v]; }
+            if (mt >= C.K) { const int x = atomicAdd(&S.ctr[C_TNX], 1); stk[2 * x] = mt; stk[2 * x + 1] = S.mo[v]; }
+        }
+    }
+    __syncwarp();
+    int np = ldr(&S.ctr[C_TNP]);
     if (lane == 0) {
-        int *stk = S.stk;
+        // blossoms: the child holding the externally matched leaf keeps that
+        // match, the other children pair up along the cycle
         const int stk_cap = 4 * C.nc + 60;
-        for (int v = 0; v < nhi; v++) {
-            if (!S.alive[v] || S.bpar[v] >= 0) continue;
-            const int mt = S.mate[v];
-            int sp = 0;
-            if (mt == MATE_BOUNDARY) {
-                S.tmpa[np] = S.ms[v]; S.tmpb[np] = -1; np++;
-            } else if (mt >= 0 && v < mt) {
-                S.tmpa[np] = S.ms[v]; S.tmpb[np] = S.mo[v]; np++;
-                stk[sp++] = mt; stk[sp++] = S.mo[v];
-            } else {
-                continue;
-            }
-            stk[sp++] = v; stk[sp++] = S.ms[v];
-            while (sp > 0) {
-                const int ext = stk[--sp];
-                const int node = stk[--sp];
-                if (node < C.K) continue;
-                const int m = S.clen[node], cb = S.cbeg[node];
-                const int c0 = ext >= 0 ? child_of(S, node, ext) : -1;
-                if (c0 < 0 || m <= 0) { S.ctr[C_ERR] |= ERR_INTERNAL; break; }
-                int i0 = 0;
-                for (int j = 0; j < m; j++) if (S.cnode[cb + j] == c0) i0 = j;
-                if (sp + 2 * m + 2 > stk_cap || np + m > 2 * C.nc) { S.ctr[C_ERR] |= ERR_CAP; break; }
-                stk[sp++] = c0; stk[sp++] = ext;
-                for (int j = 1; j < m; j += 2) {
-                    const int i1 = (i0 + j) % m, i2 = (i0 + j + 1) % m;
-                    const int lx = S.cs[cb + i1], lz = S.co[cb + i1];
-                    S.tmpa[np] = lx; S.tmpb[np] = lz; np++;
-                    stk[sp++] = S.cnode[cb + i1]; stk[sp++] = lx;
-                    stk[sp++] = S.cnode[cb + i2]; stk[sp++] = lz;
-                }
+        int sp = 2 * ldr(&S.ctr[C_TNX]);
+        while (sp > 0) {
+            const int ext = stk[--sp];
+            const int node = stk[--sp];
+            if (node < C.K) continue;
+            const int m = S.clen[node], cb = S.cbeg[node];
+            const int c0 = ext >= 0 ? child_of(S, node, ext) : -1;
+            if (c0 < 0 || m <= 0) { S.ctr[C_ERR] |= ERR_INTERNAL; break; }
+            int i0 = 0;
+            for (int j = 0; j < m; j++) if (S.cnode[cb + j] == c0) i0 = j;
+            if (sp + 2 * m + 2 > stk_cap || np + m > 2 * C.nc) { S.ctr[C_ERR] |= ERR_CAP; break; }
+            stk[sp++] = c0; stk[sp++] = ext;
+            for (int j = 1; j < m; j += 2) {
+                const int i1 = (i0 + j) % m, i2 = (i0 + j + 1) % m;
+                const int lx = S.cs[cb + i1], lz = S.co[cb + i1];
+                S.tmpa[np] = lx; S.tmpb[np] = lz; np++;
+                stk[sp++] = S.cnode[cb + i1]; stk[sp++] = lx;
+                stk[sp++] = S.cnode[cb + i2]; stk[sp++] = lz;
             }
         }
     }
@@ -1048,47 +1056,72 @@ __device__ __noinline__ int local_ball(const Slab &S, const Shot &C, int s, int 
     return settled;
 }
 
-// Level-1 neighbourhood of event s by enumeration, for graphs in which a path
-// of length <= Rb has at most two edges (DGraph::hop2): every event reached by
-// a path of one or two edges of length <= Rb is recorded through pair_upsert
-// (the minimum over those paths is the exact distance, since the shortest
-// path has at most two edges), and the boundary candidates through s itself or
-// a neighbour within Rb.  Same records as local_ball's for every use: pairs
-// within Rb exactly, and the canonical boundary contact whenever it lies within
-// Rb / 2 (a longer contact is only an upper bound, refined by the flooder
-// before a region can reach it).
-__device__ void local_2hop(const Slab &S, const Shot &C, int s, int Rb) {
+// Level-1 neighbourhoods by enumeration, for graphs in which a path of length
+// <= Rb has at most two edges (DGraph::hop2): every event reached from event s
+// by a path of one or two edges of length <= Rb is recorded through
+// pair_upsert from the lower-ranked end (the minimum over those paths is the
+// exact distance, since the shortest path has at most two edges), and the
+// boundary candidates through s itself or a neighbour within Rb go to sbnd[s].
+// Same records as local_ball's for every use: pairs within Rb exactly, and the
+// canonical boundary contact whenever it lies within Rb / 2 (a longer contact
+// is only an upper bound, refined by the flooder before a region can reach
+// it).  One lane per (event, adjacency slot of the event), numbered by a warp
+// prefix sum of the degrees.  All lanes call.
+__device__ void level1_2hop(const Slab &S, const Shot &C, int Rb, int lane) {
     const DGraph &g = C.g;
-    const int src = S.svtx[s];
-    unsigned long long bbest = EMPTY64;
-    const int r0 = __ldg(g.row + src), r1 = __ldg(g.row + src + 1);
-    for (int j = r0; j < r1; j++) {
-        const SlotV a = load_slot(g, j);
-        if (a.nbr < 0) {
-            const unsigned long long c = ((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.eid;
-            bbest = c < bbest ? c : bbest;
-            continue;
+    for (int base = 0; base < C.K; base += WS) {
+        const int s = base + lane;
+        int src = -1, r0 = 0, deg = 0;
+        if (s < C.K) {
+            src = S.svtx[s];
+            r0 = __ldg(g.row + src);
+            deg = __ldg(g.row + src + 1) - r0;
         }
-        if (a.w > Rb) continue;
-        if (is_defect(C, a.nbr)) {
-            const int f = rank_of(S, C, a.nbr);
-            if (f > s) pair_upsert(S, C, s, f, a.w);
+        int incl = deg;
+        for (int o = 1; o < WS; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
         }
-        const int q0 = __ldg(g.row + a.nbr), q1 = __ldg(g.row + a.nbr + 1);
-        for (int k = q0; k < q1; k++) {
-            const SlotV b = load_slot(g, k);
-            const int nd = a.w + b.w;
-            if (b.nbr < 0) {
-                const unsigned long long c = ((unsigned long long)(unsigned)nd << 32) | (unsigned)b.eid;
-                bbest = c < bbest ? c : bbest;
+        const int total = __shfl_sync(FULL, incl, WS - 1);
+        const int excl = incl - deg;
+        for (int t0 = 0; t0 < total; t0 += WS) {
+            const int t = t0 + lane;
+            int ow = 0;
+            for (int step = WS / 2; step > 0; step >>= 1) {
+                const int e = __shfl_sync(FULL, excl, ow + step);
+                if (e <= t) ow += step;
+            }
+            const int osrc = __shfl_sync(FULL, src, ow);
+            const int oj = __shfl_sync(FULL, r0 - excl, ow) + t;
+            if (t >= total) continue;
+            const int os = base + ow;
+            const SlotV a = load_slot(g, oj);
+            if (a.nbr < 0) {
+                atomicMin(&S.sbnd[os], ((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.eid);
                 continue;
             }
-            if (nd > Rb || b.nbr == src || !is_defect(C, b.nbr)) continue;
-            const int f = rank_of(S, C, b.nbr);
-            if (f > s) pair_upsert(S, C, s, f, nd);
+            if (a.w > Rb) continue;
+            if (is_defect(C, a.nbr)) {
+                const int f = rank_of(S, C, a.nbr);
+                if (f > os) pair_upsert(S, C, os, f, a.w);
+            }
+            unsigned long long bbest = EMPTY64;
+            const int q0 = __ldg(g.row + a.nbr), q1 = __ldg(g.row + a.nbr + 1);
+            for (int k = q0; k < q1; k++) {
+                const SlotV b = load_slot(g, k);
+                const int nd = a.w + b.w;
+                if (b.nbr < 0) {
+                    const unsigned long long c = ((unsigned long long)(unsigned)nd << 32) | (unsigned)b.eid;
+                    bbest = c < bbest ? c : bbest;
+                    continue;
+                }
+                if (nd > Rb || b.nbr == osrc || !is_defect(C, b.nbr)) continue;
+                const int f = rank_of(S, C, b.nbr);
+                if (f > os) pair_upsert(S, C, os, f, nd);
+            }
+            if (bbest != EMPTY64) atomicMin(&S.sbnd[os], bbest);
         }
     }
-    atomicMin(&S.sbnd[s], bbest);
 }
 
 // Decode one shot with hash tables scaled by `scale`; returns QEC_SHOT_* or -1
@@ -1152,11 +1185,13 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
         // canonical boundary candidate.  Events whose neighbourhood is too large for
         // the lane go through the warp-wide flooder instead.
         bool any_big = false;
-        for (int s = lane; s < K; s += WS) {
-            int r = 0;
-        if (g.hop2) local_2hop(S, C, s, g.b1);
-        else r = local_ball(S, C, s, g.b1);
-            if (r < 0) { S.cst0[s] = 1; any_big = true; } else S.cst0[s] = 0;
+        if (g.hop2) {
+            level1_2hop(S, C, g.b1, lane);
+        } else {
+            for (int s = lane; s < K; s += WS) {
+                const int r = local_ball(S, C, s, g.b1);
+                if (r < 0) { S.cst0[s] = 1; any_big = true; } else S.cst0[s] = 0;
+            }
         }
         __syncwarp();
         if (__any_sync(FULL, any_big)) {
