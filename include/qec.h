@@ -237,7 +237,7 @@ int qec_get_tuning(qec_tuning *t);
  * call before any stream capture.  Every call shares the array and zeroes its
  * work counters on `stream`: calls whose work overlaps on the GPU race, so the
  * caller must order them (for example by issuing them on one stream). */
-#define QEC_STATIC_SCRATCH_BYTES (64LL * 1024 * 1024)
+#define QEC_STATIC_SCRATCH_BYTES (80LL * 1024 * 1024)
 #define QEC_STATIC_WARPS 152
 #define QEC_STATIC_MAX_EVENTS 128
 #define QEC_STATIC_MAX_SHOTS (1 << 20)

@@ -91,6 +91,20 @@ __device__ __forceinline__ unsigned long long ldr(const unsigned long long *p) {
     return v;
 }
 
+// One explored entry: key (vertex << 32 | source) and exact distance in one
+// 16-byte slot, read by a single vector load.
+struct __align__(16) HEnt {
+    unsigned long long key;
+    int val;
+    int pad;
+};
+__device__ __forceinline__ void ld_ent(const HEnt *p, unsigned long long &k, int &v) {
+    unsigned long long a, b;
+    asm volatile("ld.relaxed.cta.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+    k = a;
+    v = (int)(unsigned)(b & 0xffffffffu);
+}
+
 // Warp-aggregated atomicAdd(ctr, 1) over the currently active lanes.
 __device__ __forceinline__ int agg_inc(int *ctr, int lane) {
     const unsigned m = __activemask();
@@ -121,10 +135,9 @@ struct Slab {
     // per detection event (source)
     int *svtx, *srad, *stop, *sR, *sbeg, *scnt, *sexh, *inplay, *comp, *cst0, *cst1, *cst2;
     unsigned long long *sbnd;
-    // explored entries: key (vertex << 32 | source), value exact distance;
-    // `ent` holds the table slots of every source's bands (band lists)
-    unsigned long long *hkey;
-    int *hval;
+    // explored entries (open addressing, keyed by vertex and source); `ent`
+    // holds the table slots of every source's bands (band lists)
+    HEnt *ht;
     int *ent;
     unsigned long long *wl0, *wl1, *tl;   // work lists (table slots) / new entries (slot << 32 | position)
     int *xsrc, *xR, *xcnt, *xcur;         // sources being extended, target radii, band counts
@@ -155,7 +168,7 @@ __host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &
     S.sexh = bump<int>(p, c.kc); S.inplay = bump<int>(p, c.kc); S.comp = bump<int>(p, c.kc);
     S.cst0 = bump<int>(p, c.kc); S.cst1 = bump<int>(p, c.kc); S.cst2 = bump<int>(p, c.kc);
     S.sbnd = bump<unsigned long long>(p, c.kc);
-    S.hkey = bump<unsigned long long>(p, c.hc); S.hval = bump<int>(p, c.hc);
+    S.ht = bump<HEnt>(p, c.hc);
     S.ent = bump<int>(p, c.ec);
     S.wl0 = bump<unsigned long long>(p, c.wc); S.wl1 = bump<unsigned long long>(p, c.wc);
     S.tl = bump<unsigned long long>(p, c.ec);
@@ -215,8 +228,10 @@ __device__ int ht_get(const Slab &S, const Shot &C, int v, int s) {
     const unsigned long long key = ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
     unsigned i = hslot(v, C.hmask);
     for (unsigned n = 0; n <= C.hmask; n++) {
-        unsigned long long k = ldr(&S.hkey[i]);
-        if (k == key) return ldr(&S.hval[i]);
+        unsigned long long k;
+        int v;
+        ld_ent(&S.ht[i], k, v);
+        if (k == key) return v;
         if (k == EMPTY64) return INF32;
         i = (i + 1) & C.hmask;
     }
@@ -229,18 +244,18 @@ __device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d, unsi
     const unsigned long long key = ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
     unsigned i = hslot(v, C.hmask);
     for (unsigned n = 0; n <= C.hmask; n++) {
-        unsigned long long k = ldr(&S.hkey[i]);
+        unsigned long long k = ldr(&S.ht[i].key);
         if (k == EMPTY64) {
-            unsigned long long prev = atomicCAS(&S.hkey[i], EMPTY64, key);
+            unsigned long long prev = atomicCAS(&S.ht[i].key, EMPTY64, key);
             if (prev == EMPTY64) {
-                atomicMin(&S.hval[i], d);
+                atomicMin(&S.ht[i].val, d);
                 slot = i;
                 return 1;
             }
             k = prev;
         }
         if (k == key) {
-            int old = atomicMin(&S.hval[i], d);
+            int old = atomicMin(&S.ht[i].val, d);
             slot = i;
             return d < old ? 2 : 0;
         }
@@ -309,11 +324,13 @@ __device__ __forceinline__ SlotV load_slot(const DGraph &g, int j) {
 __device__ void contacts_at(const Slab &S, const Shot &C, int s, int z, int base) {
     unsigned i = hslot(z, C.hmask);
     for (unsigned n = 0; n <= C.hmask; n++) {
-        unsigned long long k = ldr(&S.hkey[i]);
+        unsigned long long k;
+        int v;
+        ld_ent(&S.ht[i], k, v);
         if (k == EMPTY64) return;
         if ((int)(k >> 32) == z) {
             int s2 = (int)(unsigned)(k & 0xffffffffu);
-            if (s2 != s) pair_upsert(S, C, s, s2, base + ldr(&S.hval[i]));
+            if (s2 != s) pair_upsert(S, C, s, s2, base + v);
         }
         i = (i + 1) & C.hmask;
     }
@@ -393,8 +410,7 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
             int dx = 0, Rn = -1, r0 = 0, deg = 0, xi = 0;
             if (i < nf) {
                 const unsigned hx = F[i];
-                key = ldr(&S.hkey[hx]);
-                dx = ldr(&S.hval[hx]);
+                ld_ent(&S.ht[hx], key, dx);
                 const int x = (int)(key >> 32);
                 xi = S.xidx[(int)(unsigned)(key & 0xffffffffu)];
                 Rn = S.xR[xi];
@@ -484,9 +500,10 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
     // region and within Rad(a) + largest weight of a.
     for (int i = lane; i < nt; i += WS) {
         const unsigned hy = (unsigned)(S.tl[i] >> 32);
-        const unsigned long long key = ldr(&S.hkey[hy]);
+        unsigned long long key;
+        int dy;
+        ld_ent(&S.ht[hy], key, dy);
         const int yv = (int)(key >> 32), s = (int)(unsigned)(key & 0xffffffffu);
-        const int dy = ldr(&S.hval[hy]);
         contacts_at(S, C, s, yv, dy);
         if (yv != S.svtx[s] && is_defect(C, yv)) {
             const int f = rank_of(S, C, yv);
@@ -942,7 +959,7 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, lo
 }
 
 __device__ void clear_tables(const Slab &S, const Shot &C, int lane) {
-    for (unsigned i = lane; i <= C.hmask; i += WS) { S.hkey[i] = EMPTY64; S.hval[i] = INF32; }
+    for (unsigned i = lane; i <= C.hmask; i += WS) S.ht[i] = HEnt{EMPTY64, INF32, 0};
     for (unsigned i = lane; i <= C.pmask; i += WS) { S.pkey[i] = EMPTY64; S.pval[i] = INF32; }
     for (int i = lane; i < C_TOTAL; i += WS) S.ctr[i] = 0;
     __syncwarp();

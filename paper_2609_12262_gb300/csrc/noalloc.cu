@@ -8,7 +8,7 @@
 // milliseconds) or fail half-way for lack of memory, and an application that
 // reserves all device memory up front at start-up has nothing left to give
 // later.  For them this entry point uses only what the library already holds:
-// one static device array of QEC_STATIC_SCRATCH_BYTES (64 MiB) that every GPU
+// one static device array of QEC_STATIC_SCRATCH_BYTES (80 MiB) that every GPU
 // loading the library keeps until the process exits.  The caller still passes
 // the inputs and the outputs.
 //
