@@ -104,6 +104,21 @@ __device__ __forceinline__ void ld_ent(const HEnt *p, unsigned long long &k, int
     k = a;
     v = (int)(unsigned)(b & 0xffffffffu);
 }
+// Claim an empty entry {EMPTY64, INF32} for (key, d) with one 16-byte
+// compare-and-swap; returns true on success, else the key found there.
+__device__ __forceinline__ bool claim_ent(HEnt *p, unsigned long long key, int d, unsigned long long &found) {
+    const unsigned long long ek = ~0ull, ev = (unsigned long long)(unsigned)INT_MAX;
+    const unsigned long long nv = (unsigned long long)(unsigned)d;
+    unsigned long long ok, ov;
+    asm volatile("{\n\t.reg .b128 cmp, swp, old;\n\t"
+                 "mov.b128 cmp, {%2, %3};\n\t"
+                 "mov.b128 swp, {%4, %5};\n\t"
+                 "atom.relaxed.cta.global.cas.b128 old, [%6], cmp, swp;\n\t"
+                 "mov.b128 {%0, %1}, old;\n\t}"
+                 : "=l"(ok), "=l"(ov) : "l"(ek), "l"(ev), "l"(key), "l"(nv), "l"(p) : "memory");
+    found = ok;
+    return ok == ek && ov == ev;
+}
 
 // Warp-aggregated atomicAdd(ctr, 1) over the currently active lanes.
 __device__ __forceinline__ int agg_inc(int *ctr, int lane) {
@@ -144,8 +159,8 @@ struct Slab {
     int *xidx;                            // position of a source in xsrc during an extension
     int *wcum;                            // detection events in syndrome words before word w
     // pairs: key (lo << 32 | hi), value distance, list of used slots
-    unsigned long long *pkey;
-    int *pval, *plist;
+    HEnt *pt;
+    int *plist;
     // matcher nodes (leaf s = node s, blossoms above K)
     int *y, *bpar, *label, *tpar, *tps, *tpo, *mate, *ms, *mo, *nroot, *minleaf, *cbeg, *clen,
         *alive, *freel, *tmpa, *tmpb, *stk;
@@ -175,7 +190,7 @@ __host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &
     S.xsrc = bump<int>(p, c.kc); S.xR = bump<int>(p, c.kc); S.xcnt = bump<int>(p, c.kc); S.xcur = bump<int>(p, c.kc);
     S.xidx = bump<int>(p, c.kc);
     S.wcum = bump<int>(p, c.wcap);
-    S.pkey = bump<unsigned long long>(p, c.phc); S.pval = bump<int>(p, c.phc); S.plist = bump<int>(p, c.phc);
+    S.pt = bump<HEnt>(p, c.phc); S.plist = bump<int>(p, c.phc);
     S.y = bump<int>(p, c.nc); S.bpar = bump<int>(p, c.nc); S.label = bump<int>(p, c.nc);
     S.tpar = bump<int>(p, c.nc); S.tps = bump<int>(p, c.nc); S.tpo = bump<int>(p, c.nc);
     S.mate = bump<int>(p, c.nc); S.ms = bump<int>(p, c.nc); S.mo = bump<int>(p, c.nc);
@@ -246,13 +261,10 @@ __device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d, unsi
     for (unsigned n = 0; n <= C.hmask; n++) {
         unsigned long long k = ldr(&S.ht[i].key);
         if (k == EMPTY64) {
-            unsigned long long prev = atomicCAS(&S.ht[i].key, EMPTY64, key);
-            if (prev == EMPTY64) {
-                atomicMin(&S.ht[i].val, d);
+            if (claim_ent(&S.ht[i], key, d, k)) {
                 slot = i;
                 return 1;
             }
-            k = prev;
         }
         if (k == key) {
             int old = atomicMin(&S.ht[i].val, d);
@@ -270,20 +282,17 @@ __device__ void pair_upsert(const Slab &S, const Shot &C, int a, int b, int d) {
     const unsigned long long key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
     unsigned i = pslot(lo, hi, C.pmask);
     for (unsigned n = 0; n <= C.pmask; n++) {
-        unsigned long long k = ldr(&S.pkey[i]);
+        unsigned long long k = ldr(&S.pt[i].key);
         if (k == EMPTY64) {
-            unsigned long long prev = atomicCAS(&S.pkey[i], EMPTY64, key);
-            if (prev == EMPTY64) {
-                atomicMin(&S.pval[i], d);
+            if (claim_ent(&S.pt[i], key, d, k)) {
                 int idx = atomicAdd(&S.ctr[C_NPAIRS], 1);
                 if ((unsigned)idx * 2u > C.pmask) set_err(S, ERR_CAP);
                 else S.plist[idx] = (int)i;
                 return;
             }
-            k = prev;
         }
         if (k == key) {
-            atomicMin(&S.pval[i], d);
+            atomicMin(&S.pt[i].val, d);
             return;
         }
         i = (i + 1) & C.pmask;
@@ -296,8 +305,10 @@ __device__ int pair_get(const Slab &S, const Shot &C, int a, int b) {
     const unsigned long long key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
     unsigned i = pslot(lo, hi, C.pmask);
     for (unsigned n = 0; n <= C.pmask; n++) {
-        unsigned long long k = ldr(&S.pkey[i]);
-        if (k == key) return ldr(&S.pval[i]);
+        unsigned long long k;
+        int v;
+        ld_ent(&S.pt[i], k, v);
+        if (k == key) return v;
         if (k == EMPTY64) return INF32;
         i = (i + 1) & C.pmask;
     }
@@ -757,10 +768,12 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
         const int np = ldr(&S.ctr[C_NPAIRS]);
         for (int i = lane; i < np; i += WS) {
             const int sl = S.plist[i];
-            const unsigned long long k = ldr(&S.pkey[sl]);
+            unsigned long long k;
+            int pv;
+            ld_ent(&S.pt[sl], k, pv);
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
             const int ia = S.inplay[a], ib = S.inplay[b], A = S.stop[a], B = S.stop[b];
-            const int ra = S.srad[a], rb = S.srad[b], pv = ldr(&S.pval[sl]);
+            const int ra = S.srad[a], rb = S.srad[b];
             if (!ia || !ib || A == B) continue;
             const int r = S.label[A] + S.label[B];
             if (r <= 0) continue;
@@ -960,7 +973,7 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, lo
 
 __device__ void clear_tables(const Slab &S, const Shot &C, int lane) {
     for (unsigned i = lane; i <= C.hmask; i += WS) S.ht[i] = HEnt{EMPTY64, INF32, 0};
-    for (unsigned i = lane; i <= C.pmask; i += WS) { S.pkey[i] = EMPTY64; S.pval[i] = INF32; }
+    for (unsigned i = lane; i <= C.pmask; i += WS) S.pt[i] = HEnt{EMPTY64, INF32, 0};
     for (int i = lane; i < C_TOTAL; i += WS) S.ctr[i] = 0;
     __syncwarp();
 }
@@ -1233,8 +1246,10 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
             bool changed = false;
             for (int i = lane; i < npairs; i += WS) {
                 const int sl = S.plist[i];
-                if (ldr(&S.pval[sl]) > g.b1) continue;
-                const unsigned long long k = ldr(&S.pkey[sl]);
+                unsigned long long k;
+                int pv;
+                ld_ent(&S.pt[sl], k, pv);
+                if (pv > g.b1) continue;
                 const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
                 const int la = ldr(&S.comp[a]), lb = ldr(&S.comp[b]);
                 if (la != lb) {
@@ -1256,8 +1271,10 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
         __syncwarp();
         for (int i = lane; i < npairs; i += WS) {
             const int sl = S.plist[i];
-            if (ldr(&S.pval[sl]) > g.d1) continue;
-            const unsigned long long k = ldr(&S.pkey[sl]);
+            unsigned long long k;
+            int pv;
+            ld_ent(&S.pt[sl], k, pv);
+            if (pv > g.d1) continue;
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
             if (S.comp[a] == S.comp[b]) atomicAdd(&S.cst2[S.comp[a]], 1);
         }
