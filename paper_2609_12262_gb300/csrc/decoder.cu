@@ -259,16 +259,20 @@ __device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d, unsi
     const unsigned long long key = ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
     unsigned i = hslot(v, C.hmask);
     for (unsigned n = 0; n <= C.hmask; n++) {
-        unsigned long long k = ldr(&S.ht[i].key);
+        unsigned long long k;
+        int v;
+        ld_ent(&S.ht[i], k, v);
         if (k == EMPTY64) {
             if (claim_ent(&S.ht[i], key, d, k)) {
                 slot = i;
                 return 1;
             }
+            v = INF32;
         }
         if (k == key) {
-            int old = atomicMin(&S.ht[i].val, d);
             slot = i;
+            if (d >= v) return 0;   // values only decrease: nothing to do
+            int old = atomicMin(&S.ht[i].val, d);
             return d < old ? 2 : 0;
         }
         i = (i + 1) & C.hmask;
@@ -282,7 +286,9 @@ __device__ void pair_upsert(const Slab &S, const Shot &C, int a, int b, int d) {
     const unsigned long long key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
     unsigned i = pslot(lo, hi, C.pmask);
     for (unsigned n = 0; n <= C.pmask; n++) {
-        unsigned long long k = ldr(&S.pt[i].key);
+        unsigned long long k;
+        int v;
+        ld_ent(&S.pt[i], k, v);
         if (k == EMPTY64) {
             if (claim_ent(&S.pt[i], key, d, k)) {
                 int idx = atomicAdd(&S.ctr[C_NPAIRS], 1);
@@ -290,9 +296,10 @@ __device__ void pair_upsert(const Slab &S, const Shot &C, int a, int b, int d) {
                 else S.plist[idx] = (int)i;
                 return;
             }
+            v = INF32;
         }
         if (k == key) {
-            atomicMin(&S.pt[i].val, d);
+            if (d < v) atomicMin(&S.pt[i].val, d);
             return;
         }
         i = (i + 1) & C.pmask;
