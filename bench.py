@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--scaling", action="store_true",
                     help="scaling study: d in {25,31,41,51} x p in {.001,.003,.005}, us per round vs d")
     ap.add_argument("--scaling-shots", type=int, default=10000)
+    ap.add_argument("--configs", action="store_true",
+                    help="d=5 one-shot-per-launch and d=11 non-uniform configurations, batched vs plain vs oracle")
     ap.add_argument("--event-study", action="store_true",
                     help="parallel event count per round, hierarchical vs global, d = 9..49, p = 1e-3..1e-5")
     ap.add_argument("--study-shots", type=int, default=1024)
@@ -286,6 +288,63 @@ def scaling_study(q, args, dev):
     return rows
 
 
+def config_study(q, args, dev):
+    """The small and non-uniform configurations: d=5 (5 noisy + 1 perfect round,
+    p=0.005, 10,000 shots from seed 0) and d=11 (11 rounds, per-edge p ~
+    U[0.002, 0.006], 100,000 shots), each decoded batched (one persistent launch)
+    and plain (one launch per shot), with the CPU oracle timed on the host cores
+    beside them (the CPU baseline)."""
+    import torch
+    rows = []
+    cases = [("d5_p0.005", rotated_surface_code(5, 5, 0.005), 10000, 0, 10000),
+             ("d11_U[0.002,0.006]", rotated_surface_code(11, 11, p_range=(0.002, 0.006), p_seed=1), 100000, 1, 4000)]
+    for name, pg, S, seed, n_plain in cases:
+        syn, _ = sample_shots(pg, S, seed)
+        g = q.Graph.from_phys(pg)
+        t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
+        out = (torch.empty(S, dtype=torch.int64, device=dev), torch.empty(S, dtype=torch.int64, device=dev),
+               torch.empty(S, dtype=torch.int32, device=dev))
+        for _ in range(3):
+            q.decode_batch([g], t, num_shots=S, out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record()
+        for _ in range(reps):
+            q.decode_batch([g], t, num_shots=S, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        batch_rate = reps * S / (a.elapsed_time(b) / 1e3)
+        st = out[2].cpu().numpy()
+        po = (torch.empty(n_plain, dtype=torch.int64, device=dev), torch.empty(n_plain, dtype=torch.int64, device=dev),
+              torch.empty(n_plain, dtype=torch.int32, device=dev))
+        q.decode_plain(g, t, num_shots=min(200, n_plain), out=po)
+        torch.cuda.synchronize()
+        a.record()
+        q.decode_plain(g, t, num_shots=n_plain, out=po)
+        b.record()
+        torch.cuda.synchronize()
+        plain_rate = n_plain / (a.elapsed_time(b) / 1e3)
+        plain_same = bool(torch.equal(po[1], out[1][:n_plain]) and torch.equal(po[0], out[0][:n_plain]))
+        row = {"config": name, "shots": S, "rounds": pg.rounds, "batched_shots_per_s": batch_rate,
+               "batched_us_per_round": 1e6 / batch_rate / pg.rounds, "plain_shots_per_s": plain_rate,
+               "plain_shots": n_plain, "plain_us_per_round": 1e6 / plain_rate / pg.rounds,
+               "batched_over_plain": batch_rate / plain_rate, "plain_equals_batched": plain_same,
+               "nonzero_status": int(np.count_nonzero(st)),
+               "alg_bytes_per_shot": 4 * pg.words + 20,
+               "hbm_frac": batch_rate * (4 * pg.words + 20) / 1e9 / load_peaks()[0]}
+        if not args.no_cpu_baseline:
+            gid = np.zeros(S, np.int32)
+            offs = np.arange(S, dtype=np.int64) * pg.words
+            rate, n, secs, cores = cpu_oracle_rate([pg], gid, offs, syn.reshape(-1), args.cpu_seconds)
+            row["cpu_baseline"] = {"value": rate, "unit": "shots/s", "cores": cores, "kind": "oracle",
+                                   "sample": "%d shots of this configuration in %.1f s" % (n, secs)}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+        del t, out, po
+    return rows
+
+
 def event_study(q, args, dev):
     """Parallel event count per round (Methods, "Numerical evaluation"): E_ideal of
     the hierarchical execution and the event count of global sparse blossom, both
@@ -398,6 +457,9 @@ def main():
         return
     if args.event_study:
         event_study(q, args, torch.device("cuda", local))
+        return
+    if args.configs:
+        config_study(q, args, torch.device("cuda", local))
         return
 
     graphs, gid, offs, syn = workload(args, rank)
