@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--scaling-shots", type=int, default=10000)
     ap.add_argument("--configs", action="store_true",
                     help="d=5 one-shot-per-launch and d=11 non-uniform configurations, batched vs plain vs oracle")
+    ap.add_argument("--schedule-study", action="store_true",
+                    help="alternative cluster schedules: parallel event count, throughput, Theorem 1 check")
     ap.add_argument("--event-study", action="store_true",
                     help="parallel event count per round, hierarchical vs global, d = 9..49, p = 1e-3..1e-5")
     ap.add_argument("--study-shots", type=int, default=1024)
@@ -345,6 +347,60 @@ def config_study(q, args, dev):
     return rows
 
 
+SCHEDULE_CANDIDATES = [
+    ("alg3 q=1/10 phi_min=1/100", {}),
+    ("alg3 q=1/2 phi_min=1/10", {"q": (1, 2), "phi_min": (1, 10)}),
+    ("alg3 q=1/5 phi_min=1/20", {"q": (1, 5), "phi_min": (1, 20)}),
+    ("d1 = 2 largest edges", {"d1_edges": 2}),
+]
+# Larger level-1 buffers (d1 = 3 edges, or b1 = 3 d1) make every level-1
+# neighbourhood a search over ~1000 vertices per event: decoding then runs at
+# 10^2 - 10^3 shots/s and large shots outgrow the per-shot tables (status
+# QEC_SHOT_CAPACITY), so they are left out of the default study.
+
+
+def schedule_study(q, args, dev):
+    """Alternative processing-cluster schedules (Methods, Alg. 3 with other
+    (q, phi_min), or a custom level-1 diameter d1 with the level-1 conditions
+    kept): parallel event count per round, events resolved at level 1, batched
+    throughput, and hierarchical == global on every shot (Theorem 1)."""
+    import torch
+    rows = []
+    for d, p in ((13, 0.001), (21, 0.001), (13, 0.003)):
+        pg = rotated_surface_code(d, d, p)
+        syn, _ = sample_shots(pg, args.study_shots, args.seed + 31 * d)
+        pc = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)
+        q.set_tuning(kcap=max(64, int(pc.max() * 1.1) + 8), blocks_per_sm=-1, warps_per_block=-1)
+        t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
+        S = syn.shape[0]
+        for name, spec in SCHEDULE_CANDIDATES:
+            wi = 2 * int(pg.w.max())
+            d1 = spec["d1_edges"] * wi + 1 if "d1_edges" in spec else 0
+            b1 = spec["b1_factor"] * d1 if "b1_factor" in spec else 0
+            g = q.Graph.from_phys(pg, q=spec.get("q"), phi_min=spec.get("phi_min"), d1=d1, b1=b1)
+            o, w, st, dg = q.decode_batch_ex([g], t, mode="hier")
+            go, gw, gs, _ = q.decode_batch_ex([g], t, mode="global", diag=False)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(3):
+                q.decode_batch([g], t, num_shots=S)
+            b.record()
+            torch.cuda.synchronize()
+            dg = dg.cpu().numpy()
+            row = {"d": d, "p": p, "schedule": name, "d1": int(g.info.d_k[0]), "b1": int(g.info.b_k[0]),
+                   "e_ideal_per_round": float(dg[:, 0].mean() / d),
+                   "level1_fraction": float(dg[:, 4].sum() / max(1, dg[:, 7].sum())),
+                   "shots_per_s": 3 * S / (a.elapsed_time(b) / 1e3),
+                   "hier_vs_global_mismatch": int((~(torch.eq(o, go) & torch.eq(w, gw) & torch.eq(st, gs))).sum().item()),
+                   "nonzero_status": int(torch.count_nonzero(st).item())}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        del t
+    q.set_tuning(kcap=-1, blocks_per_sm=-1, warps_per_block=-1)
+    return rows
+
+
 def event_study(q, args, dev):
     """Parallel event count per round (Methods, "Numerical evaluation"): E_ideal of
     the hierarchical execution and the event count of global sparse blossom, both
@@ -460,6 +516,9 @@ def main():
         return
     if args.configs:
         config_study(q, args, torch.device("cuda", local))
+        return
+    if args.schedule_study:
+        schedule_study(q, args, torch.device("cuda", local))
         return
 
     graphs, gid, offs, syn = workload(args, rank)

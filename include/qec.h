@@ -58,10 +58,18 @@ typedef void *qec_cuda_stream;
 /* Algorithm 3 inputs (Methods, "Finite-size parameter schedule"):
  * q = q_num / q_den, phi_min = phi_num / phi_den, both in (0, 1).
  * NULL in qec_graph_desc means q = 1/10, phi_min = 1/100 (the paper's choice,
- * Methods "Numerical evaluation"). */
+ * Methods "Numerical evaluation") and Algorithm 3's own level 1.
+ * d1, b1 (internal units, twice the integer weights; 0 = Algorithm 3's) give a
+ * custom level-1 processing-cluster diameter and buffer: b1 must satisfy the
+ * level-1 conditions of Algorithm 3 (b1 >= d1, phi_1 = 1 > 2 d1 / b1,
+ * Phi_2(b1) >= phibar_2), otherwise the schedule is rejected (QEC_EINVAL);
+ * d1 alone takes the smallest such b1.  Higher levels follow from them by the
+ * same recursion.  Theorem 1 makes any admissible schedule return a minimum-
+ * weight matching; the parallelism it exposes differs (see QEC_DIAG_*). */
 typedef struct {
     int32_t q_num, q_den;
     int32_t phi_num, phi_den;
+    int32_t d1, b1;
 } qec_params;
 
 /* Detector graph (paper "Decoding task").  num_edges physical edges; edge i

@@ -76,7 +76,7 @@ STATUS = {0: "OK", 1: "NO_SOLUTION", 2: "BUDGET", 3: "INTERNAL", 4: "BADARG"}
 class OracleGraph:
     """Merged detector graph held by the oracle."""
 
-    def __init__(self, n, u, v, w, obs, levels: int = 6):
+    def __init__(self, n, u, v, w, obs, levels: int = 6, q=(1, 10), phi_min=(1, 100), d1=None, b1=None):
         L = lib()
         self.n = int(n)
         u = np.ascontiguousarray(u, np.int32)
@@ -90,7 +90,8 @@ class OracleGraph:
             raise ValueError("invalid graph (status %d)" % st)
         self._h = h
         self.wmax = int(L.or_graph_wmax(h))
-        d, b, _ = alg3(self.wmax, levels=levels)
+        from fractions import Fraction
+        d, b, _ = alg3(self.wmax, Fraction(*q), Fraction(*phi_min), levels=levels, d1=d1, b1=b1)
         cap = 1 << 60   # larger radii than any graph distance behave identically
         self.dk = np.asarray([min(x, cap) for x in d], np.int64)
         self.bk = np.asarray([min(x, cap) for x in b], np.int64)

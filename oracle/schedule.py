@@ -32,11 +32,15 @@ def admissible(phi_k: Fraction, d_k: int, b: int, target: Fraction) -> bool:
     return b >= d_k and b > 0 and phi_k > Fraction(2 * d_k, b) and big_phi(phi_k, d_k, b) >= target
 
 
-def alg3(w_max: int, q=Fraction(1, 10), phi_min=Fraction(1, 100), levels: int = 6):
-    """Return (d, b, phi) lists for levels 1..levels (index 0 is level 1)."""
+def alg3(w_max: int, q=Fraction(1, 10), phi_min=Fraction(1, 100), levels: int = 6, d1=None, b1=None):
+    """Return (d, b, phi) lists for levels 1..levels (index 0 is level 1).
+
+    d1 / b1 replace level 1's diameter / buffer (b1 must be admissible for
+    level 1, it need not be the smallest); later levels follow by the same
+    recursion."""
     q = Fraction(q)
     phi_min = Fraction(phi_min)
-    d = [w_max + 1]
+    d = [w_max + 1 if not d1 else int(d1)]
     phi = [Fraction(1)]
     b = []
     for k in range(1, levels + 1):
@@ -44,6 +48,14 @@ def alg3(w_max: int, q=Fraction(1, 10), phi_min=Fraction(1, 100), levels: int = 
         target = phibar(k + 1, q, phi_min)
         if not pk > target:
             raise ValueError("schedule has no admissible b at level %d" % k)
+        if k == 1 and b1:
+            bk = int(b1)
+            if not admissible(pk, dk, bk, target):
+                raise ValueError("b1 = %d is not admissible for d1 = %d" % (bk, dk))
+            b.append(bk)
+            phi.append(big_phi(pk, dk, bk))
+            d.append(3 * dk + 4 * bk + 2 * w_max)
+            continue
         # b > 2 d_k / phi_k
         lo1 = math.floor(Fraction(2 * dk) / pk) + 1
         # Phi(b) >= target  <=>  b >= ((phi+2) d / (phi - target) - (phi+1) d) / phi

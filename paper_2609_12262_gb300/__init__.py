@@ -25,7 +25,8 @@ class QecError(RuntimeError):
 
 
 class qec_params(C.Structure):
-    _fields_ = [("q_num", C.c_int32), ("q_den", C.c_int32), ("phi_num", C.c_int32), ("phi_den", C.c_int32)]
+    _fields_ = [("q_num", C.c_int32), ("q_den", C.c_int32), ("phi_num", C.c_int32), ("phi_den", C.c_int32),
+                ("d1", C.c_int32), ("b1", C.c_int32)]
 
 
 class qec_graph_desc(C.Structure):
@@ -109,12 +110,13 @@ def _ptr(a, t):
     return a.ctypes.data_as(C.POINTER(t))
 
 
-def schedule(wmax_internal: int, q=(1, 10), phi_min=(1, 100), levels: int = 8):
-    """Algorithm 3 via qec_schedule: returns (d_k list, b_k list), internal units."""
+def schedule(wmax_internal: int, q=(1, 10), phi_min=(1, 100), levels: int = 8, d1: int = 0, b1: int = 0):
+    """Algorithm 3 via qec_schedule: returns (d_k list, b_k list), internal units
+    (d1, b1 > 0: custom level-1 diameter and buffer)."""
     L = lib()
     d = np.zeros(levels, np.int64)
     b = np.zeros(levels, np.int64)
-    p = qec_params(q[0], q[1], phi_min[0], phi_min[1])
+    p = qec_params(q[0], q[1], phi_min[0], phi_min[1], int(d1), int(b1))
     n = L.qec_schedule(int(wmax_internal), C.byref(p), _ptr(d, C.c_int64), _ptr(b, C.c_int64), levels)
     if n < 1:
         raise QecError(last_error())
@@ -124,7 +126,8 @@ def schedule(wmax_internal: int, q=(1, 10), phi_min=(1, 100), levels: int = 8):
 class Graph:
     """A detector graph resident on the current CUDA device (qec_graph_create)."""
 
-    def __init__(self, num_detectors, u, v, w, obs, num_observables: int = 1, q=None, phi_min=None):
+    def __init__(self, num_detectors, u, v, w, obs, num_observables: int = 1, q=None, phi_min=None,
+                 d1: int = 0, b1: int = 0):
         L = lib()
         self._u = np.ascontiguousarray(u, np.int32)
         self._v = np.ascontiguousarray(v, np.int32)
@@ -139,10 +142,10 @@ class Graph:
         desc.w = _ptr(self._w, C.c_int32)
         desc.obs = _ptr(self._o, C.c_uint64)
         self._params = None
-        if q is not None or phi_min is not None:
+        if q is not None or phi_min is not None or d1 or b1:
             q = q or (1, 10)
             phi_min = phi_min or (1, 100)
-            self._params = qec_params(q[0], q[1], phi_min[0], phi_min[1])
+            self._params = qec_params(q[0], q[1], phi_min[0], phi_min[1], int(d1), int(b1))
             desc.params = C.pointer(self._params)
         h = C.c_void_p()
         _check(L.qec_graph_create(C.byref(desc), C.byref(h)))

@@ -136,9 +136,13 @@ int admissible(Q phi, long long d, long long b, Q target) {
 }
 
 // Algorithm 3 (Methods, "Finite-size parameter schedule"), internal units.
-int schedule(int wmax, Q q, Q phimin, long long *dk, long long *bk, int maxlev) {
+// d1c / b1c > 0 replace the level-1 diameter / buffer (b1c must be admissible
+// for level 1: b >= d, phi_1 = 1 > 2d/b, Phi_2(b) >= phibar_2); the schedule
+// continues from them by the same recursion.
+int schedule(int wmax, Q q, Q phimin, long long *dk, long long *bk, int maxlev, long long d1c = 0,
+             long long b1c = 0) {
     Q phi = qint(1);
-    long long d = (long long)wmax + 1;
+    long long d = d1c > 0 ? d1c : (long long)wmax + 1;
     int lev = 0;
     for (int k = 1; k <= maxlev; k++) {
         // phibar_{k+1} = phimin + (1 - phimin) q^k
@@ -165,8 +169,13 @@ int schedule(int wmax, Q q, Q phimin, long long *dk, long long *bk, int maxlev) 
         if (b < 1) b = 1;
         if (b > (__int128)(1LL << 61)) break;
         long long bl = (long long)b;
-        if (admissible(phi, d, bl, target) != 1) break;
-        if (bl - 1 >= 1 && admissible(phi, d, bl - 1, target) != 0) break;
+        if (k == 1 && b1c > 0) {
+            if (admissible(phi, d, b1c, target) != 1) break;   // a custom b_1 need not be the smallest
+            bl = b1c;
+        } else {
+            if (admissible(phi, d, bl, target) != 1) break;
+            if (bl - 1 >= 1 && admissible(phi, d, bl - 1, target) != 0) break;
+        }
         dk[lev] = d;
         bk[lev] = bl;
         lev++;
@@ -322,15 +331,19 @@ int qec_schedule(int32_t wmax_internal, const qec_params *params, int64_t *d_k, 
     if (wmax_internal < 1 || !d_k || !b_k || max_levels < 1 || max_levels > 64)
         return fail(QEC_EINVAL, "bad schedule arguments");
     Q q = {1, 10}, phimin = {1, 100};
+    long long d1c = 0, b1c = 0;
     if (params) {
         if (params->q_den <= 0 || params->phi_den <= 0 || params->q_num <= 0 || params->phi_num <= 0 ||
             params->q_num >= params->q_den || params->phi_num >= params->phi_den)
             return fail(QEC_EINVAL, "params must be fractions in (0, 1)");
+        if (params->d1 < 0 || params->b1 < 0) return fail(QEC_EINVAL, "negative level-1 override");
         mk(params->q_num, params->q_den, q);
         mk(params->phi_num, params->phi_den, phimin);
+        d1c = params->d1;
+        b1c = params->b1;
     }
     std::vector<long long> dk((size_t)max_levels), bk((size_t)max_levels);
-    const int lev = schedule(wmax_internal, q, phimin, dk.data(), bk.data(), max_levels);
+    const int lev = schedule(wmax_internal, q, phimin, dk.data(), bk.data(), max_levels, d1c, b1c);
     for (int i = 0; i < lev; i++) { d_k[i] = dk[i]; b_k[i] = bk[i]; }
     return lev >= 1 ? lev : fail(QEC_EINVAL, "no admissible level-1 parameters");
 }
@@ -346,13 +359,17 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
         return fail(QEC_EINVAL, "num_observables out of range");
     if (m > 0 && (!desc->u || !desc->v || !desc->w || !desc->obs)) return fail(QEC_EINVAL, "edge array is NULL");
     Q q = {1, 10}, phimin = {1, 100};
+    long long d1c = 0, b1c = 0;
     if (desc->params) {
         const qec_params *p = desc->params;
         if (p->q_den <= 0 || p->phi_den <= 0 || p->q_num <= 0 || p->phi_num <= 0 || p->q_num >= p->q_den ||
             p->phi_num >= p->phi_den)
             return fail(QEC_EINVAL, "params must be fractions in (0, 1)");
+        if (p->d1 < 0 || p->b1 < 0) return fail(QEC_EINVAL, "negative level-1 override");
         mk(p->q_num, p->q_den, q);
         mk(p->phi_num, p->phi_den, phimin);
+        d1c = p->d1;
+        b1c = p->b1;
     }
     const unsigned long long obs_mask =
         desc->num_observables >= 64 ? ~0ull : ((1ull << desc->num_observables) - 1ull);
@@ -391,7 +408,7 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
         delete g;
         return fail(QEC_ERANGE, "largest weight x detectors exceeds 2^30 (distances are int32)");
     }
-    g->num_levels = schedule(g->wmax, q, phimin, g->dk, g->bk, 8);
+    g->num_levels = schedule(g->wmax, q, phimin, g->dk, g->bk, 8, d1c, b1c);
     if (g->num_levels < 1) {
         delete g;
         return fail(QEC_EINVAL, "Algorithm 3 schedule has no admissible level-1 parameters");

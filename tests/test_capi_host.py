@@ -49,6 +49,30 @@ def test_schedule_custom_params(L):
     assert d == od and b == ob
 
 
+@pytest.mark.parametrize("kw", [dict(d1=373), dict(d1=373, b1=800), dict(d1=559, q=(1, 50), phi_min=(1, 1000)),
+                                dict(b1=1000), dict(d1=187, b1=375)])
+def test_schedule_custom_level1(L, kw):
+    from fractions import Fraction
+    qq, pm = kw.get("q", (1, 10)), kw.get("phi_min", (1, 100))
+    d, b = q.schedule(186, q=qq, phi_min=pm, levels=3, d1=kw.get("d1", 0), b1=kw.get("b1", 0))
+    od, ob, _ = alg3(186, Fraction(*qq), Fraction(*pm), levels=len(d), d1=kw.get("d1"), b1=kw.get("b1"))
+    assert len(d) >= 2 and d == od and b == ob
+    if "d1" in kw:
+        assert d[0] == kw["d1"]
+    if "b1" in kw:
+        assert b[0] == kw["b1"]
+
+
+@pytest.mark.parametrize("d1,b1", [(373, 746), (373, 372), (187, 300)])
+def test_schedule_rejects_inadmissible_level1(L, d1, b1):
+    """phi_1 = 1 > 2 d1 / b1 fails for b1 <= 2 d1: both sides refuse the schedule."""
+    from fractions import Fraction
+    with pytest.raises(q.QecError):
+        q.schedule(186, levels=3, d1=d1, b1=b1)
+    with pytest.raises(ValueError):
+        alg3(186, Fraction(1, 10), Fraction(1, 100), levels=3, d1=d1, b1=b1)
+
+
 def _desc(n, u, v, w, o, nobs=1):
     arrs = [np.ascontiguousarray(u, np.int32), np.ascontiguousarray(v, np.int32),
             np.ascontiguousarray(w, np.int32), np.ascontiguousarray(o, np.uint64)]

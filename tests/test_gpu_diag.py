@@ -139,3 +139,34 @@ def test_event_study_sizes_sampled(qd, d, p, shots, check):
             got = (int(W[i]), int(O[i]), int(S[i])) + tuple(int(D[i, COL[f]]) for f in FIELDS)
             exp = (r["weight"], r["obs"], r["status"]) + tuple(int(r[f]) for f in FIELDS)
             assert got == exp, (d, p, mode, i, got, exp)
+
+
+SCHED = [("d1=2 edges", dict(d1=2)), ("d1=3 edges", dict(d1=3)), ("d1=2 edges, wide b1", dict(d1=2, b1_factor=3)),
+         ("q=1/2, phi_min=1/10", dict(q=(1, 2), phi_min=(1, 10)))]
+
+
+@pytest.mark.parametrize("sname,spec", SCHED, ids=[s[0] for s in SCHED])
+def test_custom_schedule_matches_oracle(qd, sname, spec):
+    """Alternative cluster schedules: the GPU under a custom schedule equals the
+    oracle under the same schedule (results and parallel event counts) and the
+    global run (Theorem 1)."""
+    from tests.test_theorem1 import schedule_kw
+    for pg, shots, seed in ((rotated_surface_code(9, 9, 0.005), 600, 51),
+                            (rotated_surface_code(11, 11, p_range=(0.002, 0.006), p_seed=1), 300, 52),
+                            (rotated_surface_code(7, 7, 0.02), 300, 53)):
+        kw = schedule_kw(pg, spec)
+        og = OracleGraph.from_phys(pg, **kw)
+        g = qd.Graph.from_phys(pg, q=kw.get("q"), phi_min=kw.get("phi_min"), d1=kw.get("d1", 0),
+                               b1=kw.get("b1", 0))
+        assert int(g.info.d_k[0]) == int(og.dk[0]) and int(g.info.b_k[0]) == int(og.bk[0])
+        syn, _ = sample_shots(pg, shots, seed)
+        W, O, S, D = run(qd, [g], syn, "hier")
+        gw, go, gs, _ = run(qd, [g], syn, "global")
+        assert np.array_equal(W, gw) and np.array_equal(O, go)
+        for i in range(shots):
+            r = og.diag(unpack_defects(syn[i], pg.num_detectors), "hier")
+            if r["clusters_above_l1"] > 1:
+                continue
+            got = (int(W[i]), int(O[i]), int(S[i])) + tuple(int(D[i, COL[f]]) for f in FIELDS)
+            exp = (r["weight"], r["obs"], r["status"]) + tuple(int(r[f]) for f in FIELDS)
+            assert got == exp, (sname, i, got, exp)

@@ -25,6 +25,7 @@ CASES = [
 
 @pytest.mark.parametrize("name,kw,shots", CASES, ids=[c[0] for c in CASES])
 def test_global_equals_hierarchical(name, kw, shots):
+    kw = dict(kw)
     d = kw.pop("d")
     g = rotated_surface_code(d, d, **kw)
     og = OracleGraph.from_phys(g)
@@ -42,3 +43,44 @@ def test_global_equals_hierarchical(name, kw, shots):
         implodes += a.events_implode
     if "blossoms" in name:
         assert implodes > 0
+
+
+# Alternative schedules: custom level-1 diameters (one, two and three edges of
+# the largest weight) and other (q, phi_min).  Theorem 1 holds for any
+# admissible schedule, so every candidate must reproduce global sparse blossom.
+SCHEDULES = [
+    ("d1=2 edges", dict(d1=2)),
+    ("d1=3 edges", dict(d1=3)),
+    ("d1=2 edges, wide b1", dict(d1=2, b1_factor=3)),
+    ("q=1/2, phi_min=1/10", dict(q=(1, 2), phi_min=(1, 10))),
+    ("q=1/50, phi_min=1/1000", dict(q=(1, 50), phi_min=(1, 1000))),
+]
+
+
+def schedule_kw(g, spec):
+    """Oracle-graph keyword arguments for a schedule spec on graph g."""
+    wmax_internal = 2 * int(g.w.max())
+    kw = {k: v for k, v in spec.items() if k in ("q", "phi_min")}
+    if "d1" in spec:
+        kw["d1"] = spec["d1"] * wmax_internal + 1
+        if "b1_factor" in spec:
+            kw["b1"] = spec["b1_factor"] * kw["d1"]
+    return kw
+
+
+@pytest.mark.parametrize("sname,spec", SCHEDULES, ids=[s[0] for s in SCHEDULES])
+@pytest.mark.parametrize("name,kw,shots", [CASES[0], CASES[1], CASES[3]], ids=[CASES[i][0] for i in (0, 1, 3)])
+def test_alternative_schedules_equal_global(sname, spec, name, kw, shots):
+    kw = dict(kw)
+    d = kw.pop("d")
+    g = rotated_surface_code(d, d, **kw)
+    og = OracleGraph.from_phys(g, **schedule_kw(g, spec))
+    ref = OracleGraph.from_phys(g)
+    syn, _ = sample_shots(g, min(shots, 400), 23)
+    for s in range(syn.shape[0]):
+        det = unpack_defects(syn[s], g.num_detectors)
+        a = ref.decode(det, "global")
+        b = og.decode(det, "hier")
+        assert b.status == 0 and (a.weight, a.obs) == (b.weight, b.obs), (sname, s, det.tolist())
+        assert b.dual_feasible and b.tight and b.dual_sum == b.primal_internal
+        assert b.touch_violations == 0
