@@ -228,12 +228,14 @@ struct Shot {
     int nm, ncut, tcut, tlast, nx;
 };
 
+// Home slots: the high bits of a multiplicative (Fibonacci) hash, so that
+// nearby vertices spread over the whole table; mask + 1 is a power of two.
 __device__ __forceinline__ unsigned hslot(int v, unsigned mask) {
-    return ((unsigned)v * 2654435761u) & mask;
+    return ((unsigned)v * 2654435761u) >> (32 - __popc(mask));
 }
 
 __device__ __forceinline__ unsigned pslot(int lo, int hi, unsigned mask) {
-    return (((unsigned)lo * 2654435761u) ^ ((unsigned)hi * 2246822519u)) & mask;
+    return (((unsigned)lo * 2654435761u + (unsigned)hi) * 2246822519u) >> (32 - __popc(mask));
 }
 
 __device__ __forceinline__ void set_err(const Slab &S, int bit) { atomicOr(&S.ctr[C_ERR], bit); }
