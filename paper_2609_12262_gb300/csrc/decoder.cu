@@ -416,11 +416,13 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
     }
     __syncwarp();
     int nf = min(ldr(&S.ctr[C_WL]), C.wc);
+    // only this warp appends during the relaxation: the list counters live in
+    // registers (warp-uniform) and each round's appends are placed by ballot
+    int ntl = ldr(&S.ctr[C_TL]);
+    const unsigned lt = (1u << lane) - 1u;
     for (int iter = 0;; iter++) {
         if (iter >= 4096) { if (lane == 0) set_err(S, ERR_INTERNAL); break; }
-        __syncwarp();
-        if (lane == 0) S.ctr[C_WL] = 0;
-        __syncwarp();
+        int nwl = 0;
         // one lane per (work item, adjacency slot): items are taken 32 at a
         // time, their slots numbered by a warp prefix sum of the degrees, and
         // slot t goes to lane t mod 32 (its item found by binary search)
@@ -457,31 +459,36 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
                 const int oRn = __shfl_sync(FULL, Rn, ow);
                 const int oj = __shfl_sync(FULL, r0 - excl, ow) + t;
                 const int oxi = __shfl_sync(FULL, xi, ow);
-                if (t >= total) continue;
-                const int s = (int)(unsigned)(okey & 0xffffffffu);
-                const SlotV sl = load_slot(g, oj);
-                const int nd = odx + sl.w;
-                if (sl.nbr < 0) { bnd_update(S, s, nd, sl.eid); continue; }
-                if (nd > oRn) continue;
-                unsigned hs;
-                const int r = ht_upsert(S, C, sl.nbr, s, nd, hs);
+                int r = 0;
+                unsigned hs = 0;
+                if (t < total) {
+                    const int s = (int)(unsigned)(okey & 0xffffffffu);
+                    const SlotV sl = load_slot(g, oj);
+                    const int nd = odx + sl.w;
+                    if (sl.nbr < 0) bnd_update(S, s, nd, sl.eid);
+                    else if (nd <= oRn) r = ht_upsert(S, C, sl.nbr, s, nd, hs);
+                }
+                const unsigned mt = __ballot_sync(FULL, r == 1);
+                const unsigned mw = __ballot_sync(FULL, r >= 1);
                 if (r == 1) {
-                    const int e = agg_inc(&S.ctr[C_TL], lane);
+                    const int e = ntl + __popc(mt & lt);
                     if (e < C.ec) S.tl[e] = ((unsigned long long)hs << 32) | (unsigned)oxi; else set_err(S, ERR_CAP);
                 }
                 if (r >= 1) {
-                    const int w = agg_inc(&S.ctr[C_WL], lane);
+                    const int w = nwl + __popc(mw & lt);
                     if (w < C.wc) Wn[w] = hs; else set_err(S, ERR_CAP);
                 }
+                ntl += __popc(mt);
+                nwl += __popc(mw);
             }
         }
         __syncwarp();
-        const int nw = ldr(&S.ctr[C_WL]);
         const int err = ldr(&S.ctr[C_ERR]);
-        if (nw == 0 || err) break;
-        nf = min(nw, C.wc);
+        if (nwl == 0 || err) break;
+        nf = min(nwl, C.wc);
         unsigned *t = F; F = Wn; Wn = t;
     }
+    if (lane == 0) S.ctr[C_TL] = ntl;
     __syncwarp();
     const int nt = min(ldr(&S.ctr[C_TL]), C.ec);
     const int e0 = ldr(&S.ctr[C_ECOUNT]);
