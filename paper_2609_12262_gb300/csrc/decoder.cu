@@ -339,23 +339,6 @@ __device__ __forceinline__ SlotV load_slot(const DGraph &g, int j) {
     return s;
 }
 
-// Record every pair (s, s') whose balls meet at vertex z: `base` is the
-// distance from s to z through the edge being examined.
-__device__ void contacts_at(const Slab &S, const Shot &C, int s, int z, int base) {
-    unsigned i = hslot(z, C.hmask);
-    for (unsigned n = 0; n <= C.hmask; n++) {
-        unsigned long long k;
-        int v;
-        ld_ent(&S.ht[i], k, v);
-        if (k == EMPTY64) return;
-        if ((int)(k >> 32) == z) {
-            int s2 = (int)(unsigned)(k & 0xffffffffu);
-            if (s2 != s) pair_upsert(S, C, s, s2, base + v);
-        }
-        i = (i + 1) & C.hmask;
-    }
-}
-
 __device__ __forceinline__ bool is_defect(const Shot &C, int v) {
     return (__ldg(C.row + (v >> 5)) >> (v & 31)) & 1u;
 }
@@ -525,16 +508,49 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
     // pair of regions at the instant they become tight: on a shortest path
     // between them, the first vertex at distance >= Rad(a) from a lies in b's
     // region and within Rad(a) + largest weight of a.
-    for (int i = lane; i < nt; i += WS) {
-        const unsigned hy = (unsigned)(S.tl[i] >> 32);
-        unsigned long long key;
-        int dy;
-        ld_ent(&S.ht[hy], key, dy);
-        const int yv = (int)(key >> 32), s = (int)(unsigned)(key & 0xffffffffu);
-        contacts_at(S, C, s, yv, dy);
-        if (yv != S.svtx[s] && is_defect(C, yv)) {
-            const int f = rank_of(S, C, yv);
-            if (f >= 0 && f != s) pair_upsert(S, C, s, f, dy);
+    // Each lane walks the probe chain of one entry, one probe per round; a lane
+    // whose walk has ended takes the next unwalked entry, so the warp's lanes
+    // stay busy however the chain lengths vary.
+    {
+        const unsigned lt = (1u << lane) - 1u;
+        int cur = -1, yv = 0, s = 0, dy = 0;
+        unsigned pos = 0, nprobe = 0;
+        int next = 0;
+        for (long long round = 0; round < (long long)nt * (C.hmask + 2) + 1; round++) {
+            const unsigned idle = __ballot_sync(FULL, cur < 0);
+            if (cur < 0) {
+                const int k = next + __popc(idle & lt);
+                if (k < nt) {
+                    cur = k;
+                    const unsigned hy = (unsigned)(S.tl[k] >> 32);
+                    unsigned long long key;
+                    ld_ent(&S.ht[hy], key, dy);
+                    yv = (int)(key >> 32);
+                    s = (int)(unsigned)(key & 0xffffffffu);
+                    pos = hslot(yv, C.hmask);
+                    nprobe = 0;
+                    if (yv != S.svtx[s] && is_defect(C, yv)) {
+                        const int f = rank_of(S, C, yv);
+                        if (f >= 0 && f != s) pair_upsert(S, C, s, f, dy);
+                    }
+                }
+            }
+            next += __popc(idle);
+            if (!__any_sync(FULL, cur >= 0)) break;
+            if (cur >= 0) {
+                unsigned long long k;
+                int v;
+                ld_ent(&S.ht[pos], k, v);
+                if (k == EMPTY64 || ++nprobe > C.hmask) {
+                    cur = -1;
+                } else {
+                    if ((int)(k >> 32) == yv) {
+                        const int s2 = (int)(unsigned)(k & 0xffffffffu);
+                        if (s2 != s) pair_upsert(S, C, s, s2, dy + v);
+                    }
+                    pos = (pos + 1) & C.hmask;
+                }
+            }
         }
     }
     __syncwarp();
