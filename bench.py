@@ -26,6 +26,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -83,6 +84,35 @@ def workload(args, rank):
     from paper_2609_12262_gb300.replicas import shard_seed
     graphs, gid, offs, syn = mixed_batch(DS, args.shots_per_d, args.p, seed=shard_seed(args.seed, rank))
     return graphs, gid, offs, syn
+
+
+PROFILE = os.path.join(ROOT, "profiles", "batch_kernel_mixed_d7-21_p003.md")
+KERNEL_SOURCES = ["decoder.cu", "qec_internal.h", "capi.cpp"]
+
+
+def kernel_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2609_12262_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(shots):
+    """DRAM bytes per launch of the main pass from the committed ncu summary
+    (per shot, scaled to this launch's shots), or None when the kernel sources
+    changed since the counters were taken."""
+    try:
+        text = open(PROFILE).read()
+        per_shot = float(re.search(r"dram_bytes_per_shot:\s*([0-9.]+)", text).group(1))
+        sha = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", text).group(1)
+    except Exception:
+        return None, "no ncu summary"
+    if sha != kernel_sha256():
+        return None, "kernel changed since the ncu capture"
+    return per_shot * shots, "ncu dram__bytes_read.sum + dram__bytes_write.sum per shot x shots (%s)" % \
+        os.path.relpath(PROFILE, ROOT)
 
 
 def load_peaks():
@@ -577,6 +607,7 @@ def main():
     alg_bytes = int(4 * words.sum() + S * (4 + 8) + S * (8 + 8 + 4))
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (statistics.mean(launch_ms) / 1000.0) / 1e9
+    traffic, traffic_note = measured_traffic(S)
     mean_d = float(np.mean(np.array(DS)[gid]))
 
     # plain one-shot-per-launch path on a subsample
@@ -664,11 +695,13 @@ def main():
             "tuning": q.get_tuning(),
             "autotuned": {k: tuned[k] for k in ("candidates", "ms", "shots")} if tuned else None,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind,
-                         "note": "algorithmic bytes: syndrome rows + shot metadata + outputs per launch"},
+                         "note": "algorithmic bytes: syndrome rows + shot metadata + outputs per launch; "
+                                 "traffic: " + traffic_note},
             "clocks": clocks,
-            "gpu_launches": 2 * args.steps,
+            # per step: graph sort (count, scan, scatter) for a mixed batch, main pass, overflow pass
+            "gpu_launches": (5 if len(graphs) > 1 else 2) * args.steps,
             "e2e": e2e,
             "serving": serving,
             "cpu_baseline": cpu,

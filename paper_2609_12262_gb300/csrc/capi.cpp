@@ -207,6 +207,7 @@ struct Workspace {
     unsigned long long *queue = nullptr;
     int *overflow = nullptr;
     int *order = nullptr;          // graph-sorted work order of a mixed batch
+    bool fill1 = false, fill2 = false;   // slabs to fill with ones before the next launch
     int *gcnt = nullptr;           // 64 ints: per-graph counts and cursors
     long long overflow_cap = 0;
     cudaEvent_t done = nullptr;
@@ -263,6 +264,10 @@ int ws_ensure(Workspace &w, int dev, const SlabCaps &caps, long long nwarps, con
         e = cudaEventSynchronize(w.done);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
     }
+    // the kernel expects every explored / pair table entry to be all ones on
+    // entry and leaves it so; a new allocation or a new slab layout is filled
+    if (grow1 || std::memcmp(&w.caps, &caps, sizeof(caps)) != 0) w.fill1 = true;
+    if (grow2 || std::memcmp(&w.caps2, &caps2, sizeof(caps2)) != 0) w.fill2 = true;
     if (grow1) {
         if (w.slabs) cudaFree(w.slabs);
         w.slabs = nullptr;
@@ -590,6 +595,16 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     if (rc != QEC_OK) return rc;
     ce = cudaStreamWaitEvent(s, w.done, 0);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamWaitEvent");
+    if (w.fill1) {
+        ce = cudaMemsetAsync(w.slabs, 0xff, (size_t)(w.slab_bytes * w.nwarps), s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemsetAsync");
+        w.fill1 = false;
+    }
+    if (w.fill2) {
+        ce = cudaMemsetAsync(w.slabs2, 0xff, (size_t)(w.slab_bytes2 * w.nwarps2), s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemsetAsync");
+        w.fill2 = false;
+    }
     BatchArgs a;
     std::memset(&a, 0, sizeof(a));
     for (int i = 0; i < num_graphs; i++) a.g[i] = graphs[i]->dg;

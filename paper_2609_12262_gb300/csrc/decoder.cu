@@ -104,10 +104,10 @@ __device__ __forceinline__ void ld_ent(const HEnt *p, unsigned long long &k, int
     k = a;
     v = (int)(unsigned)(b & 0xffffffffu);
 }
-// Claim an empty entry {EMPTY64, INF32} for (key, d) with one 16-byte
+// Claim an empty entry (all 16 bytes ones) for (key, d) with one 16-byte
 // compare-and-swap; returns true on success, else the key found there.
 __device__ __forceinline__ bool claim_ent(HEnt *p, unsigned long long key, int d, unsigned long long &found) {
-    const unsigned long long ek = ~0ull, ev = (unsigned long long)(unsigned)INT_MAX;
+    const unsigned long long ek = ~0ull, ev = ~0ull;   // an empty entry is all ones
     const unsigned long long nv = (unsigned long long)(unsigned)d;
     unsigned long long ok, ov;
     asm volatile("{\n\t.reg .b128 cmp, swp, old;\n\t"
@@ -1003,10 +1003,26 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, lo
     obs = o;
 }
 
+// Per-shot counters; the tables themselves are already empty (release_tables).
 __device__ void clear_tables(const Slab &S, const Shot &C, int lane) {
-    for (unsigned i = lane; i <= C.hmask; i += WS) S.ht[i] = HEnt{EMPTY64, INF32, 0};
-    for (unsigned i = lane; i <= C.pmask; i += WS) S.pt[i] = HEnt{EMPTY64, INF32, 0};
     for (int i = lane; i < C_TOTAL; i += WS) S.ctr[i] = 0;
+    __syncwarp();
+}
+
+// Return the explored and pair tables to empty: the slots recorded in the band
+// lists (every explored entry) and the pair list (every pair), or with `all`
+// the whole region of this attempt's table sizes.
+__device__ __noinline__ void release_tables(const Slab &S, const Shot &C, int lane, bool all) {
+    __syncwarp();
+    const HEnt e = HEnt{EMPTY64, -1, -1};
+    if (all) {
+        for (unsigned i = lane; i <= C.hmask; i += WS) S.ht[i] = e;
+        for (unsigned i = lane; i <= C.pmask; i += WS) S.pt[i] = e;
+    } else {
+        const int ne = ldr(&S.ctr[C_ECOUNT]), np = ldr(&S.ctr[C_NPAIRS]);
+        for (int i = lane; i < ne; i += WS) S.ht[S.ent[i] & C.hmask] = e;
+        for (int i = lane; i < np; i += WS) S.pt[S.plist[i] & C.pmask] = e;
+    }
     __syncwarp();
 }
 
@@ -1188,10 +1204,9 @@ __device__ void level1_2hop(const Slab &S, const Shot &C, int Rb, int lane) {
 
 // Decode one shot with hash tables scaled by `scale`; returns QEC_SHOT_* or -1
 // when the working set overflowed (retry with a larger scale).
-__device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
-                              int lane, unsigned scale, unsigned long long deadline, long long &w_out,
-                              unsigned long long &o_out, int *dg) {
-    Shot C;
+__device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
+                                   int lane, unsigned scale, unsigned long long deadline, long long &w_out,
+                                   unsigned long long &o_out, int *dg, Shot &C) {
     C.g = g;
     C.ec = A.caps.ec; C.wc = A.caps.wc; C.cc = A.caps.cc;
     C.band = max(g.wmax, 1) * max(A.band_factor, 1);
@@ -1410,6 +1425,21 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
         dg[QEC_DIAG_DEFECTS] = K;
     }
     return QEC_SHOT_OK;
+}
+
+// One decode attempt.  The explored and pair tables are empty (all-ones) on
+// entry and are returned empty: after a successful shot only the slots listed
+// in the band lists and the pair list are reset, after anything else the
+// whole region the attempt could have used.
+__device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
+                              int lane, unsigned scale, unsigned long long deadline, long long &w_out,
+                              unsigned long long &o_out, int *dg) {
+    Shot C;
+    C.hmask = 0;
+    C.pmask = 0;
+    const int st = decode_attempt_body(A, S, g, row, lane, scale, deadline, w_out, o_out, dg, C);
+    if (C.hmask) release_tables(S, C, lane, st != QEC_SHOT_OK);
+    return st;
 }
 
 __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, int lane,

@@ -78,6 +78,7 @@ int qec_decode_batch_static(const qec_graph *const *graphs, int32_t num_graphs, 
     if (kQueueBytes + kOverflowBytes + slab * kWarps > kScratchBytes)
         return err(QEC_ERANGE, "static scratch too small for its slabs");
     char *base = nullptr;
+    bool fill = false;
     {
         // set-up, once per device, with that device current
         std::lock_guard<std::mutex> lk(g_mu);
@@ -89,10 +90,16 @@ int qec_decode_batch_static(const qec_graph *const *graphs, int32_t num_graphs, 
                 return err(QEC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
             s.base = static_cast<char *>(p);
             s.ready = true;
+            fill = true;
         }
         base = s.base;
     }
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (fill) {
+        // the kernel expects empty (all-ones) table entries and leaves them so
+        ce = cudaMemsetAsync(base + kQueueBytes + kOverflowBytes, 0xff, (size_t)(slab * kWarps), st);
+        if (ce != cudaSuccess) return err(QEC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(ce));
+    }
     auto *queue = reinterpret_cast<unsigned long long *>(base);
     ce = cudaMemsetAsync(queue, 0, 4 * sizeof(unsigned long long), st);   // counters start at zero
     if (ce != cudaSuccess) return err(QEC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(ce));

@@ -116,7 +116,10 @@ bool alloc_slot(qec_stream *st, Slot &s) {
               cudaMalloc(&s.slabs, (size_t)(st->sb * st->nwarps)) == cudaSuccess &&
               cudaMalloc(&s.slabs2, (size_t)(st->sb2 * st->nwarps2)) == cudaSuccess &&
               cudaMalloc(&s.queue, 4 * sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMalloc(&s.overflow, R * 4) == cudaSuccess;
+              cudaMalloc(&s.overflow, R * 4) == cudaSuccess &&
+              // the kernel expects empty (all-ones) table entries and leaves them so
+              cudaMemset(s.slabs, 0xff, (size_t)(st->sb * st->nwarps)) == cudaSuccess &&
+              cudaMemset(s.slabs2, 0xff, (size_t)(st->sb2 * st->nwarps2)) == cudaSuccess;
     return ok;
 }
 
