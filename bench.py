@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="small workload (profiling)")
     ap.add_argument("--kcap", type=int, default=0, help="detection events per main-pass slab (0 = auto)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
-    ap.add_argument("--serve-seconds", type=float, default=2.5, help="serving run length (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving run length (0 = skip); 5 s = 10^6 windows at 200k/s")
     ap.add_argument("--serve-rate", type=float, default=200000.0, help="Poisson arrival rate, windows/s")
     ap.add_argument("--scaling", action="store_true",
                     help="scaling study: d in {25,31,41,51} x p in {.001,.003,.005}, us per round vs d")
