@@ -99,20 +99,45 @@ def kernel_sha256():
     return h.hexdigest()
 
 
-def measured_traffic(shots):
-    """DRAM bytes per launch of the main pass from the committed ncu summary
-    (per shot, scaled to this launch's shots), or None when the kernel sources
-    changed since the counters were taken."""
+def profile_figure(name):
+    """A per-shot figure of the committed ncu summary, or None when it is missing
+    or the kernel sources changed since the counters were taken."""
     try:
         text = open(PROFILE).read()
-        per_shot = float(re.search(r"dram_bytes_per_shot:\s*([0-9.]+)", text).group(1))
+        value = float(re.search(name + r":\s*([0-9.]+)", text).group(1))
         sha = re.search(r"kernel_sources_sha256:\s*([0-9a-f]{64})", text).group(1)
     except Exception:
         return None, "no ncu summary"
     if sha != kernel_sha256():
         return None, "kernel changed since the ncu capture"
-    return per_shot * shots, "ncu dram__bytes_read.sum + dram__bytes_write.sum per shot x shots (%s)" % \
-        os.path.relpath(PROFILE, ROOT)
+    return value, os.path.relpath(PROFILE, ROOT)
+
+
+def measured_traffic(shots):
+    """DRAM bytes per launch of the main pass (per shot from the ncu summary,
+    scaled to this launch's shots), or None."""
+    per_shot, src = profile_figure("dram_bytes_per_shot")
+    if per_shot is None:
+        return None, src
+    return per_shot * shots, "ncu dram__bytes_read.sum + dram__bytes_write.sum per shot x shots (%s)" % src
+
+
+# Issue peak of the GB300: 152 SMs x 4 warp schedulers x 1 warp-instruction per
+# clock x 2.07 GHz (largest SM clock).
+ISSUE_PEAK = 152 * 4 * 2.07e9
+
+
+def alu_roofline(shots, launch_s):
+    """Secondary roofline: warp instructions issued per second (instruction count
+    per shot from the ncu summary, live launch time) against the issue peak."""
+    per_shot, src = profile_figure("warp_instructions_per_shot")
+    if per_shot is None:
+        return None
+    achieved = per_shot * shots / launch_s
+    return {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "warp-instructions/s",
+            "frac": achieved / ISSUE_PEAK,
+            "note": "smsp__inst_executed per shot (%s) x shots / CUDA-event launch time; peak = 152 SMs x 4 "
+                    "schedulers x 2.07 GHz" % src}
 
 
 def load_peaks():
@@ -699,6 +724,7 @@ def main():
                          "peak_source": peak_kind,
                          "note": "algorithmic bytes: syndrome rows + shot metadata + outputs per launch; "
                                  "traffic: " + traffic_note},
+            "roofline_alu": alu_roofline(S, statistics.mean(launch_ms) / 1000.0),
             "clocks": clocks,
             # per step: graph sort (count, scan, scatter) for a mixed batch, main pass, overflow pass
             "gpu_launches": (5 if len(graphs) > 1 else 2) * args.steps,
