@@ -1255,6 +1255,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     // level-1 critical path (stopping time, event count), clusters, events
     // resolved at level 1, events of all level-1 runs
     int t1 = 0, e1 = 0, ncl1 = 0, nres1 = 0, ntot = 0;
+    int gr = K;   // next level-1 cluster (its lowest event) that needs the event loop
     if (A.mode == QEC_MODE_HIERARCHICAL) {
         // ---- Algorithm 1, level 1: every event's neighbourhood within b_1 by a
         // lane-local Dijkstra (each lane its own events): pairs within b_1 with their
@@ -1367,41 +1368,42 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         e1 = ncl1 > 0 ? 1 : 0;
         ntot = ncl1;
         need_general = __any_sync(FULL, need_general);
-        if (need_general) {
-            for (int r = 0; r < K; r++) {
-                if (S.comp[r] != r || !(S.cst1[r] & 2)) continue;
-                for (int s = lane; s < K; s += WS)
-                    if (S.comp[s] == r) make_root(S, s);
-                __syncwarp();
-                C.nm = 0; C.tlast = 0;
-                const int st = run_matcher(S, C, lane, nhi);
-                if (st != RUN_OK) {
-                    if (st == RUN_CAP) return -1;
-                    return st == RUN_NOSOL ? QEC_SHOT_NO_SOLUTION
-                           : st == RUN_BUDGET ? QEC_SHOT_BUDGET_EXCEEDED : QEC_SHOT_INTERNAL;
-                }
-                for (int s = lane; s < K; s += WS)
-                    if (S.comp[s] == r) S.inplay[s] = 0;
-                __syncwarp();
-                e1 = max(e1, C.nm); t1 = max(t1, C.tlast); ntot += C.nm; ncl1++; nres1 += S.cst0[r];
+        gr = need_general ? 0 : K;
+    }
+    // ---- level-1 clusters without a closed form, one run each (from an empty
+    // state apart from themselves), then the top level: every remaining event
+    // from t = 0 with the stopped level-1 configurations present as frozen
+    // regions (global mode: every event, from an empty state).  One call site
+    // of the event loop serves both, which keeps the kernel's hot code small.
+    for (int guard = 0; guard <= K + 1; guard++) {
+        while (gr < K && (S.comp[gr] != gr || !(S.cst1[gr] & 2))) gr++;
+        const bool top = gr >= K;
+        if (top) {
+            for (int s = lane; s < K; s += WS) {
+                if (S.alive[s] || S.stop[s] != s) S.inplay[s] = 1;   // stopped level-1 configuration
+                else make_root(S, s);
             }
+            C.ncut = 0;
+            C.tcut = t1;
+        } else {
+            for (int s = lane; s < K; s += WS)
+                if (S.comp[s] == gr) make_root(S, s);
         }
-    }
-    // ---- top level: every remaining event from t = 0, level-1 states frozen
-    // (global mode: every event, from an empty state)
-    for (int s = lane; s < K; s += WS) {
-        if (S.alive[s] || S.stop[s] != s) S.inplay[s] = 1;   // stopped level-1 configuration
-        else make_root(S, s);
-    }
-    __syncwarp();
-    C.nm = 0; C.ncut = 0; C.tlast = 0; C.tcut = t1;
-    {
+        __syncwarp();
+        C.nm = 0;
+        C.tlast = 0;
         const int st = run_matcher(S, C, lane, nhi);
         if (st != RUN_OK) {
             if (st == RUN_CAP) return -1;
             return st == RUN_NOSOL ? QEC_SHOT_NO_SOLUTION
                    : st == RUN_BUDGET ? QEC_SHOT_BUDGET_EXCEEDED : QEC_SHOT_INTERNAL;
         }
+        if (top) break;
+        for (int s = lane; s < K; s += WS)
+            if (S.comp[s] == gr) S.inplay[s] = 0;
+        __syncwarp();
+        e1 = max(e1, C.nm); t1 = max(t1, C.tlast); ntot += C.nm; ncl1++; nres1 += S.cst0[gr];
+        gr++;
     }
     long long wint = 0;
     unsigned long long ob = 0;
