@@ -36,9 +36,10 @@
 // capacities end a shot with a status code instead of spinning.
 //
 // The rarely taken matcher steps (augment, blossom, shatter), the tracing and
-// the bounded level-1 search are kept out of line (__noinline__): the event
-// loop and the flooder stay inlined, and the kernel's hot code stays small
-// enough for the instruction cache.
+// the level-1 neighbourhood searches are kept out of line (__noinline__): the
+// event loop and the flooder stay inlined, and the kernel's hot code stays
+// small enough for the instruction cache (each choice measured on the full
+// batch; inlining the flooder or moving it out of line are both slower).
 
 #include <algorithm>
 #include <climits>
@@ -1145,7 +1146,7 @@ __device__ __noinline__ int local_ball(const Slab &S, const Shot &C, int s, int 
 // is only an upper bound, refined by the flooder before a region can reach
 // it).  One lane per (event, adjacency slot of the event), numbered by a warp
 // prefix sum of the degrees.  All lanes call.
-__device__ void level1_2hop(const Slab &S, const Shot &C, int Rb, int lane) {
+__device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, int lane) {
     const DGraph &g = C.g;
     for (int base = 0; base < C.K; base += WS) {
         const int s = base + lane;
