@@ -150,8 +150,9 @@ int qec_graph_merged_edges(const qec_graph *g, int32_t *u, int32_t *v, int32_t *
  *
  * The call enqueues work and returns without synchronising.  Scratch memory
  * comes from a library-owned workspace on the device, grown on first use
- * (that growth synchronises the device once); calls that share the workspace
- * are serialised on their streams by the library.  Errors: QEC_EINVAL (null
+ * (that growth synchronises the device once, and a new workspace layout is
+ * initialised by one asynchronous fill on `stream`); calls that share the
+ * workspace are serialised on their streams by the library.  Errors: QEC_EINVAL (null
  * output pointers, num_graphs out of range, graphs on another device),
  * QEC_ENOMEM, QEC_ECUDA. num_shots == 0 is a no-op. */
 int qec_decode_batch(const qec_graph *const *graphs, int32_t num_graphs,
