@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--scaling-shots", type=int, default=10000)
     ap.add_argument("--configs", action="store_true",
                     help="d=5 one-shot-per-launch and d=11 non-uniform configurations, batched vs plain vs oracle")
+    ap.add_argument("--stream-study", action="store_true",
+                    help="sliding-window decoding of long histories (W = 2d, C = d) vs whole-history decoding")
     ap.add_argument("--schedule-study", action="store_true",
                     help="alternative cluster schedules: parallel event count, throughput, Theorem 1 check")
     ap.add_argument("--event-study", action="store_true",
@@ -402,6 +404,60 @@ def config_study(q, args, dev):
     return rows
 
 
+def stream_study(q, args, dev):
+    """Sliding-window decoding of long histories: R = 10 d noisy rounds (+ 1
+    perfect), windows of W = 2d layers every C = d layers, p = 0.003, many
+    streams per launch.  Reports rounds decoded per second and us per round for
+    the batch of streams, the latency per round of one stream decoded window
+    after window, and whole-history decoding (one window) of the same streams."""
+    import torch
+    from paper_2609_12262_gb300.window import SlidingWindow
+    rows = []
+    for d, S in ((11, 20000), (15, 8000), (21, 3000)):
+        R = 10 * d
+        pg = rotated_surface_code(d, R, 0.003)
+        syn, _ = sample_shots(pg, S, args.seed + d)
+        t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
+        dec = SlidingWindow(pg, 2 * d, d)
+        whole = q.Graph.from_phys(pg)
+        q.set_tuning(kcap=max(64, int(np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1).max()) + 8),
+                     blocks_per_sm=-1, warps_per_block=-1)
+        dec.decode(t, S)
+        q.decode_batch([whole], t, num_shots=S)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        obs, st = dec.decode(t, S)
+        b.record()
+        torch.cuda.synchronize()
+        ms_sw = a.elapsed_time(b)
+        a.record()
+        wo, ww, ws = q.decode_batch([whole], t, num_shots=S)
+        b.record()
+        torch.cuda.synchronize()
+        ms_whole = a.elapsed_time(b)
+        one = t[:pg.words * 1]
+        dec.decode(one, 1)
+        torch.cuda.synchronize()
+        a.record()
+        dec.decode(one, 1)
+        b.record()
+        torch.cuda.synchronize()
+        ms_one = a.elapsed_time(b)
+        row = {"d": d, "rounds": R, "W": 2 * d, "C": d, "p": 0.003, "streams": S, "windows": len(dec.windows),
+               "sliding_rounds_per_s": S * R / (ms_sw / 1e3), "sliding_us_per_round": ms_sw * 1e3 / (S * R),
+               "whole_history_rounds_per_s": S * R / (ms_whole / 1e3),
+               "one_stream_us_per_round": ms_one * 1e3 / R,
+               "same_observable_as_whole": float((obs == wo).double().mean().item()),
+               "sliding_nonzero_status": int(torch.count_nonzero(st).item()),
+               "whole_nonzero_status": int(torch.count_nonzero(ws).item())}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+        del t
+    q.set_tuning(kcap=-1, blocks_per_sm=-1, warps_per_block=-1)
+    return rows
+
+
 SCHEDULE_CANDIDATES = [
     ("alg3 q=1/10 phi_min=1/100", {}),
     ("alg3 q=1/2 phi_min=1/10", {"q": (1, 2), "phi_min": (1, 10)}),
@@ -574,6 +630,9 @@ def main():
         return
     if args.schedule_study:
         schedule_study(q, args, torch.device("cuda", local))
+        return
+    if args.stream_study:
+        stream_study(q, args, torch.device("cuda", local))
         return
 
     graphs, gid, offs, syn = workload(args, rank)

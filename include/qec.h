@@ -206,6 +206,58 @@ int qec_decode_batch_ex(const qec_graph *const *graphs, int32_t num_graphs,
                         uint64_t *obs_out, int64_t *weight_out, int32_t *status_out,
                         int32_t *diag_out, qec_cuda_stream stream);
 
+/* ------------------------------------------------------ sliding windows --
+ * Streaming decoding in overlapping windows (the paper's introduction: in
+ * sliding-window decoding the windows are processed one after another, so the
+ * time per syndrome round sets the throughput).  The caller cuts a long
+ * syndrome history into windows of W detector layers every C layers; a window's
+ * graph is the induced subgraph of the stream graph on its layers, and its
+ * commit region is its first C layers (every layer for the last window).  The
+ * window's correction -- the union of the canonical shortest paths of its
+ * matching (one per matched pair, one to the boundary per boundary match) -- is
+ * committed on every edge that touches the commit region: the committed
+ * observable accumulates, and each committed edge whose other endpoint lies
+ * outside the region flips that detector, which the next window's syndrome
+ * takes over (qec_window_assemble).  Every detector lies in exactly one commit
+ * region, so the committed edges of all windows together correct the whole
+ * history's syndrome. */
+
+/* Mark the detectors of g's commit region: detector_bitmap is a host array of
+ * words_per_shot(g) uint32 words (bit i = detector i), copied before return;
+ * NULL removes the region (and waits for the device to be idle).  Errors:
+ * QEC_EINVAL, QEC_ENOMEM, QEC_ECUDA. */
+int qec_graph_set_commit_region(qec_graph *g, const uint32_t *detector_bitmap);
+
+/* Decode one window of a batch of streams (Alg. 1 + Alg. 2, as
+ * qec_decode_batch).  Every graph needs a commit region (QEC_EINVAL otherwise).
+ * commit_obs_inout  device [num_shots] uint64: the committed observable of
+ *                   each shot is XORed into it.
+ * carry_out         device uint32 rows laid out like `syndromes` (same
+ *                   offsets): the detectors flipped by committed edges that
+ *                   leave the commit region (all zero for a failed shot).
+ * status_inout      device [num_shots] int32: set to the QEC_SHOT_* failure of
+ *                   a shot that fails, left unchanged otherwise (initialise to
+ *                   QEC_SHOT_OK once per stream).
+ * Other arguments, errors and the asynchronous behaviour are those of
+ * qec_decode_batch. */
+int qec_decode_window_batch(const qec_graph *const *graphs, int32_t num_graphs,
+                            const int32_t *graph_of_shot, const int64_t *syn_offset_words,
+                            const uint32_t *syndromes, int64_t num_shots,
+                            uint64_t *commit_obs_inout, uint32_t *carry_out, int32_t *status_inout,
+                            qec_cuda_stream stream);
+
+/* Window syndromes from stream syndromes, on the device: bit i of window row r
+ * is bit (bit_begin + i) of stream row r for i < nbits (0 beyond), XOR bit
+ * (carry_bit_begin + i) of carry row r for i < carry_bits when carry_rows is
+ * not NULL.  Rows: stream_rows [num_rows][stream_words], carry_rows
+ * [num_rows][carry_words], window_rows [num_rows][window_words] (all device
+ * uint32).  Errors: QEC_EINVAL (negative sizes, NULL buffers), QEC_ERANGE
+ * (nbits or carry_bits beyond the window row), QEC_ECUDA. */
+int qec_window_assemble(const uint32_t *stream_rows, int64_t stream_words, int64_t bit_begin, int32_t nbits,
+                        const uint32_t *carry_rows, int64_t carry_words, int64_t carry_bit_begin,
+                        int32_t carry_bits, uint32_t *window_rows, int64_t window_words, int64_t num_rows,
+                        qec_cuda_stream stream);
+
 /* Same as qec_decode_batch for one shot per kernel launch: shot s is decoded
  * by its own launch of a one-warp grid (the plain per-shot GPU path). */
 int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_shots,

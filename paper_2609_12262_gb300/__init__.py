@@ -79,6 +79,10 @@ def lib():
     L.qec_decode_batch.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.qec_decode_batch_ex.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, C.c_int32, vp, vp, vp, vp, vp]
     L.qec_decode_plain.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
+    L.qec_graph_set_commit_region.argtypes = [vp, vp]
+    L.qec_decode_window_batch.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+    L.qec_window_assemble.argtypes = [vp, C.c_int64, C.c_int64, C.c_int32, vp, C.c_int64, C.c_int64, C.c_int32,
+                                      vp, C.c_int64, C.c_int64, vp]
     L.qec_decode_batch_static.argtypes = [P(vp), C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
     L.qec_stream_create.argtypes = [C.c_size_t, C.c_int32, P(vp)]
     L.qec_stream_submit.argtypes = [vp, vp, vp, C.c_uint64]
@@ -159,6 +163,16 @@ class Graph:
     @classmethod
     def from_phys(cls, g, **kw):
         return cls(g.num_detectors, g.u, g.v, g.w, g.obs, **kw)
+
+    def set_commit_region(self, bitmap=None):
+        """qec_graph_set_commit_region: uint32 detector bitmap (words_per_shot words) or None."""
+        if bitmap is None:
+            _check(lib().qec_graph_set_commit_region(self._h, None))
+            return
+        b = np.ascontiguousarray(bitmap, np.uint32)
+        if b.shape[0] < self.words:
+            raise QecError("commit bitmap shorter than a syndrome row")
+        _check(lib().qec_graph_set_commit_region(self._h, C.c_void_p(b.ctypes.data)))
 
     @property
     def handle(self):
@@ -255,6 +269,30 @@ def decode_batch_ex(graphs, syndromes, graph_of_shot=None, syn_offset_words=None
                                      _dptr(syndromes), int(num_shots), MODES[mode], _dptr(obs), _dptr(w),
                                      _dptr(st), _dptr(dg), _stream_handle(stream)))
     return obs, w, st, dg
+
+
+def decode_window_batch(graphs, syndromes, commit_obs, carry, status, graph_of_shot=None, syn_offset_words=None,
+                        num_shots=None, stream=None):
+    """qec_decode_window_batch on torch device tensors: commit_obs (int64 [S],
+    XOR-accumulated), carry (int32, laid out like syndromes), status (int32 [S],
+    failures only)."""
+    if isinstance(graphs, Graph):
+        graphs = [graphs]
+    if num_shots is None:
+        num_shots = int(graph_of_shot.shape[0]) if graph_of_shot is not None else \
+            int(syndromes.numel() // graphs[0].words)
+    arr = (C.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    _check(lib().qec_decode_window_batch(arr, len(graphs), _dptr(graph_of_shot), _dptr(syn_offset_words),
+                                         _dptr(syndromes), int(num_shots), _dptr(commit_obs), _dptr(carry),
+                                         _dptr(status), _stream_handle(stream)))
+
+
+def window_assemble(stream_rows, stream_words, bit_begin, nbits, window_rows, window_words, num_rows,
+                    carry_rows=None, carry_words=0, carry_bit_begin=0, carry_bits=0, stream=None):
+    """qec_window_assemble on torch device tensors (int32 views of uint32 rows)."""
+    _check(lib().qec_window_assemble(_dptr(stream_rows), int(stream_words), int(bit_begin), int(nbits),
+                                     _dptr(carry_rows), int(carry_words), int(carry_bit_begin), int(carry_bits),
+                                     _dptr(window_rows), int(window_words), int(num_rows), _stream_handle(stream)))
 
 
 def decode_batch_static(graphs, syndromes, graph_of_shot=None, syn_offset_words=None, num_shots=None,

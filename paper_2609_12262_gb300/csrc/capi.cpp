@@ -36,6 +36,7 @@ struct qec_graph {
     int *d_seid = nullptr;
     unsigned long long *d_eobs = nullptr;
     int2 *d_eend = nullptr;
+    unsigned *d_commit = nullptr;   // commit-region bitmap (sliding windows)
     DGraph dg{};
 };
 
@@ -486,7 +487,35 @@ int qec_graph_destroy(qec_graph *g) {
     if (g->d_eobs) cudaFree(g->d_eobs);
     if (g->d_eend) cudaFree(g->d_eend);
     if (g->d_seid) cudaFree(g->d_seid);
+    if (g->d_commit) cudaFree(g->d_commit);
     delete g;
+    return QEC_OK;
+}
+
+int qec_graph_set_commit_region(qec_graph *g, const uint32_t *detector_bitmap) {
+    if (!g) return fail(QEC_EINVAL, "NULL graph");
+    cudaError_t ce;
+    if (!detector_bitmap) {
+        if (g->d_commit) {
+            ce = cudaDeviceSynchronize();   // no decode may still read it
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaDeviceSynchronize");
+            cudaFree(g->d_commit);
+        }
+        g->d_commit = nullptr;
+        g->dg.commit = nullptr;
+        return QEC_OK;
+    }
+    std::vector<unsigned> bits((size_t)g->words, 0u);
+    for (int i = 0; i < g->words; i++) bits[(size_t)i] = detector_bitmap[i];
+    if (g->n % 32) bits[(size_t)(g->n / 32)] &= (1u << (g->n % 32)) - 1u;   // detectors only
+    for (int i = g->n / 32 + (g->n % 32 ? 1 : 0); i < g->words; i++) bits[(size_t)i] = 0u;
+    if (!g->d_commit) {
+        ce = cudaMalloc(&g->d_commit, sizeof(unsigned) * (size_t)g->words);
+        if (ce != cudaSuccess) { g->d_commit = nullptr; return fail(QEC_ENOMEM, "cudaMalloc"); }
+    }
+    ce = cudaMemcpy(g->d_commit, bits.data(), sizeof(unsigned) * (size_t)g->words, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemcpy");
+    g->dg.commit = g->d_commit;
     return QEC_OK;
 }
 
@@ -552,13 +581,16 @@ int qec_release_workspace(void) {
 static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, const int32_t *graph_of_shot,
                          const int64_t *syn_offset_words, const uint32_t *syndromes, int64_t num_shots,
                          uint64_t *obs_out, int64_t *weight_out, int32_t *status_out, qec_cuda_stream stream,
-                         bool plain, int32_t mode = QEC_MODE_HIERARCHICAL, int32_t *diag_out = nullptr) {
+                         bool plain, int32_t mode = QEC_MODE_HIERARCHICAL, int32_t *diag_out = nullptr,
+                         uint64_t *commit_obs = nullptr, uint32_t *carry_out = nullptr) {
     if (num_shots < 0) return fail(QEC_EINVAL, "num_shots < 0");
     if (mode != QEC_MODE_HIERARCHICAL && mode != QEC_MODE_GLOBAL) return fail(QEC_EINVAL, "unknown mode");
+    const bool window = carry_out != nullptr;
     if (num_shots == 0) return QEC_OK;
     if (!graphs || num_graphs < 1 || num_graphs > QEC_MAX_GRAPHS_PER_BATCH)
         return fail(QEC_EINVAL, "num_graphs out of range");
-    if (!syndromes || !obs_out || !weight_out || !status_out) return fail(QEC_EINVAL, "NULL buffer");
+    if (!syndromes || !status_out || (window ? !commit_obs : (!obs_out || !weight_out)))
+        return fail(QEC_EINVAL, "NULL buffer");
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
@@ -567,6 +599,7 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     for (int i = 0; i < num_graphs; i++) {
         if (!graphs[i]) return fail(QEC_EINVAL, "NULL graph");
         if (graphs[i]->device != dev) return fail(QEC_EINVAL, "graph lives on another device");
+        if (window && !graphs[i]->d_commit) return fail(QEC_EINVAL, "graph has no commit region");
         nmax = std::max(nmax, graphs[i]->n);
     }
     qec_tuning tune;
@@ -623,6 +656,8 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     a.watchdog_ns = 60LL * 1000 * 1000 * 1000;
     a.mode = mode;
     a.diag_out = diag_out;
+    a.cobs = reinterpret_cast<unsigned long long *>(commit_obs);
+    a.carry = carry_out;
     if (plain) {
         a.slabs = w.slabs;
         a.slab_bytes = w.slab_bytes;
@@ -679,6 +714,35 @@ int qec_decode_batch_ex(const qec_graph *const *graphs, int32_t num_graphs, cons
                         qec_cuda_stream stream) {
     return decode_common(graphs, num_graphs, graph_of_shot, syn_offset_words, syndromes, num_shots, obs_out,
                          weight_out, status_out, stream, false, mode, diag_out);
+}
+
+int qec_decode_window_batch(const qec_graph *const *graphs, int32_t num_graphs, const int32_t *graph_of_shot,
+                            const int64_t *syn_offset_words, const uint32_t *syndromes, int64_t num_shots,
+                            uint64_t *commit_obs_inout, uint32_t *carry_out, int32_t *status_inout,
+                            qec_cuda_stream stream) {
+    if (!carry_out) return fail(QEC_EINVAL, "NULL buffer");
+    return decode_common(graphs, num_graphs, graph_of_shot, syn_offset_words, syndromes, num_shots, nullptr,
+                         nullptr, status_inout, stream, false, QEC_MODE_HIERARCHICAL, nullptr, commit_obs_inout,
+                         carry_out);
+}
+
+int qec_window_assemble(const uint32_t *stream_rows, int64_t stream_words, int64_t bit_begin, int32_t nbits,
+                        const uint32_t *carry_rows, int64_t carry_words, int64_t carry_bit_begin,
+                        int32_t carry_bits, uint32_t *window_rows, int64_t window_words, int64_t num_rows,
+                        qec_cuda_stream stream) {
+    if (num_rows < 0 || stream_words < 0 || window_words < 0 || bit_begin < 0 || nbits < 0 ||
+        (carry_rows && (carry_words <= 0 || carry_bit_begin < 0 || carry_bits < 0)))
+        return fail(QEC_EINVAL, "negative size");
+    if (num_rows == 0 || window_words == 0) return QEC_OK;
+    if (!stream_rows || !window_rows) return fail(QEC_EINVAL, "NULL buffer");
+    if ((long long)nbits > window_words * 32 || (carry_rows && (long long)carry_bits > window_words * 32))
+        return fail(QEC_ERANGE, "window row too short");
+    const cudaError_t ce = qec::launch_window_assemble(stream_rows, stream_words, bit_begin, nbits, carry_rows,
+                                                       carry_words, carry_bit_begin, carry_bits, window_rows,
+                                                       window_words, num_rows,
+                                                       reinterpret_cast<cudaStream_t>(stream));
+    if (ce != cudaSuccess) return cuda_fail(ce, "window assemble launch");
+    return QEC_OK;
 }
 
 int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_shots, uint64_t *obs_out,

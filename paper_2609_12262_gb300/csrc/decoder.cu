@@ -892,6 +892,8 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
 __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int dx, int lane) {
     const DGraph &g = C.g;
     for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]); n++) extend_one(S, C, s, lane);
+    // a ball that outgrew the tables: the attempt is retried with larger ones
+    if (ldr(&S.ctr[C_ERR])) return 0;
     unsigned long long o = 0;
     const int src = S.svtx[s];
     int cur = x, dcur = dx;
@@ -966,6 +968,7 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, lo
     }
     np = __shfl_sync(FULL, np, 0);
     __syncwarp();
+    if (lane == 0) S.ctr[C_TNP] = np;   // leaf pairs in tmpa / tmpb, read by commit_trace
     long long w = 0;
     unsigned long long o = 0;
     for (int i = lane; i < np; i += WS) {
@@ -1002,6 +1005,78 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, lo
     }
     wint = w;
     obs = o;
+}
+
+__device__ __forceinline__ bool in_commit(const DGraph &g, int v) {
+    return (__ldg(g.commit + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+// Canonical path from source s's vertex to vertex x at distance dx (the path
+// of path_obs): the XOR of the observables of its edges that touch the commit
+// region; each such edge with its other endpoint outside the region flips that
+// endpoint in `carry` (lane 0 writes).  All lanes call.
+__device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, int dx, int lane, unsigned *carry) {
+    const DGraph &g = C.g;
+    for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]); n++) extend_one(S, C, s, lane);
+    // a ball that outgrew the tables: the attempt is retried with larger ones
+    if (ldr(&S.ctr[C_ERR])) return 0;
+    unsigned long long o = 0;
+    const int src = S.svtx[s];
+    int cur = x, dcur = dx;
+    for (int n = 0; n < 1 << 22 && cur != src; n++) {
+        const int r0 = __ldg(g.row + cur), r1 = __ldg(g.row + cur + 1);
+        unsigned long long best = EMPTY64;
+        for (int j = r0 + lane; j < r1; j += WS) {
+            SlotV sl = load_slot(g, j);
+            if (sl.nbr < 0) continue;
+            const int dy = ht_get(S, C, sl.nbr, s);
+            if (dy != INF32 && dy + sl.w == dcur)
+                best = min(best, ((unsigned long long)(unsigned)__ldg(g.seid + j) << 32) | (unsigned)sl.nbr);
+        }
+        best = warp_min64(best);
+        if (best == EMPTY64) { if (lane == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
+        const int e = (int)(best >> 32);
+        const int nxt = (int)(unsigned)(best & 0xffffffffu);
+        const bool ci = in_commit(g, cur), ni = in_commit(g, nxt);
+        if (ci || ni) {
+            o ^= __ldg(g.eobs + e);
+            if (ci != ni && lane == 0) {
+                const int out = ci ? nxt : cur;
+                carry[out >> 5] ^= 1u << (out & 31);
+            }
+        }
+        cur = nxt;
+        dcur = ht_get(S, C, cur, s);
+    }
+    return o;
+}
+
+// Sliding-window commit of a decoded shot (the leaf pairs left by trace): the
+// correction is the union of the canonical matching paths (and boundary
+// edges); every edge that touches the graph's commit region is committed.
+// Returns the committed observable; the shot's carry row receives the
+// detectors outside the region flipped by committed edges.  All lanes call.
+__device__ __noinline__ unsigned long long commit_trace(const Slab &S, Shot &C, int lane, unsigned *carry) {
+    const DGraph &g = C.g;
+    for (int w = lane; w < g.words; w += WS) carry[w] = 0u;
+    __syncwarp();
+    const int np = ldr(&S.ctr[C_TNP]);
+    unsigned long long o = 0;
+    for (int i = 0; i < np && !ldr(&S.ctr[C_ERR]); i++) {
+        const int a = S.tmpa[i], b = S.tmpb[i];
+        if (b < 0) {
+            const unsigned long long bb = ldr(&S.sbnd[a]);
+            const int e = (int)(unsigned)(bb & 0xffffffffu);
+            const int2 ue = __ldg(g.eend + e);
+            if (in_commit(g, ue.x)) o ^= __ldg(g.eobs + e);   // the boundary edge itself
+            o ^= path_commit(S, C, a, ue.x, (int)(bb >> 32) - ue.y, lane, carry);
+        } else {
+            const int lo = min(a, b), hi = max(a, b);
+            o ^= path_commit(S, C, lo, S.svtx[hi], pair_get(S, C, lo, hi), lane, carry);
+        }
+    }
+    __syncwarp();
+    return o;
 }
 
 // Per-shot counters; the tables themselves are already empty (release_tables).
@@ -1205,6 +1280,9 @@ __device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, i
 
 // Decode one shot with hash tables scaled by `scale`; returns QEC_SHOT_* or -1
 // when the working set overflowed (retry with a larger scale).
+// WIN: sliding-window mode (BatchArgs::carry set), compiled as its own kernel so
+// that the ordinary kernel carries none of its code.
+template <bool WIN>
 __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
                                    int lane, unsigned scale, unsigned long long deadline, long long &w_out,
                                    unsigned long long &o_out, int *dg, Shot &C) {
@@ -1225,6 +1303,8 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     if (K == 0) {
         w_out = 0; o_out = 0;
         if (dg && lane < QEC_DIAG_FIELDS) dg[lane] = 0;   // no detection event: E_ideal = 0
+        if constexpr (WIN)
+            for (int w = lane; w < g.words; w += WS) A.carry[(row - A.syn) + w] = 0u;
         return QEC_SHOT_OK;
     }
     if (K > ID_MAX - 1 || 2 * K + 8 > A.caps.nc) return -2;
@@ -1409,6 +1489,9 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     long long wint = 0;
     unsigned long long ob = 0;
     trace(S, C, lane, nhi, wint, ob);
+    if constexpr (WIN) {   // sliding window: the committed part
+        if (!ldr(&S.ctr[C_ERR])) ob = commit_trace(S, C, lane, A.carry + (row - A.syn));
+    }
     const int err = ldr(&S.ctr[C_ERR]);
     if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
     w_out = wint / 2;
@@ -1434,17 +1517,19 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
 // entry and are returned empty: after a successful shot only the slots listed
 // in the band lists and the pair list are reset, after anything else the
 // whole region the attempt could have used.
+template <bool WIN>
 __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
                               int lane, unsigned scale, unsigned long long deadline, long long &w_out,
                               unsigned long long &o_out, int *dg) {
     Shot C;
     C.hmask = 0;
     C.pmask = 0;
-    const int st = decode_attempt_body(A, S, g, row, lane, scale, deadline, w_out, o_out, dg, C);
+    const int st = decode_attempt_body<WIN>(A, S, g, row, lane, scale, deadline, w_out, o_out, dg, C);
     if (C.hmask) release_tables(S, C, lane, st != QEC_SHOT_OK);
     return st;
 }
 
+template <bool WIN>
 __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, int lane,
                             unsigned long long deadline) {
     int gi = A.graph_of_shot ? A.graph_of_shot[shot] : 0;
@@ -1457,10 +1542,11 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, i
     unsigned long long o = 0;
     int *dg = A.diag_out ? A.diag_out + shot * QEC_DIAG_FIELDS : nullptr;
     for (unsigned scale = 1; scale <= 64 && status == -1; scale *= 4)
-        status = decode_attempt(A, S, g, row, lane, scale, deadline, w, o, dg);
+        status = decode_attempt<WIN>(A, S, g, row, lane, scale, deadline, w, o, dg);
+    const bool retried = status < 0 && A.pass == 0 && A.single_shot < 0;   // goes to the overflow pass
     if (status < 0) {
         status = QEC_SHOT_CAPACITY;
-        if (A.pass == 0 && A.single_shot < 0 && lane == 0) {
+        if (retried && lane == 0) {
             const unsigned long long idx = atomicAdd(&A.queue[1], 1ull);
             A.overflow[idx] = (int)shot;
         }
@@ -1468,7 +1554,15 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, i
         o = 0;
     }
     if (dg && status != QEC_SHOT_OK && lane < QEC_DIAG_FIELDS) dg[lane] = 0;
-    if (lane == 0) {
+    if constexpr (WIN) {
+        // sliding window: nothing is committed by a failed shot
+        if (status != QEC_SHOT_OK)
+            for (int i = lane; i < g.words; i += WS) A.carry[off + i] = 0u;
+        if (lane == 0) {
+            if (status == QEC_SHOT_OK) A.cobs[shot] ^= o;
+            else if (!retried) A.st_out[shot] = status;
+        }
+    } else if (lane == 0) {
         A.w_out[shot] = w;
         A.obs_out[shot] = o;
         A.st_out[shot] = status;
@@ -1476,6 +1570,7 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, i
     __syncwarp();
 }
 
+template <bool WIN>
 __global__ void __launch_bounds__(128, QEC_MIN_BLOCKS) batch_kernel(const __grid_constant__ BatchArgs a) {
     const int lane = threadIdx.x & 31;
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1487,7 +1582,7 @@ __global__ void __launch_bounds__(128, QEC_MIN_BLOCKS) batch_kernel(const __grid
         deadline = __shfl_sync(FULL, t0, 0) + (unsigned long long)a.watchdog_ns;
     }
     if (a.single_shot >= 0) {
-        if (wid == 0) decode_shot(a, S, a.single_shot, lane, deadline);
+        if (wid == 0) decode_shot<WIN>(a, S, a.single_shot, lane, deadline);
         return;
     }
     unsigned long long *counter = a.queue + (a.pass == 0 ? 0 : 2);
@@ -1499,7 +1594,7 @@ __global__ void __launch_bounds__(128, QEC_MIN_BLOCKS) batch_kernel(const __grid
         if ((long long)item >= limit) break;
         const long long shot = a.pass == 0 ? (a.order ? (long long)a.order[item] : (long long)item)
                                            : (long long)a.overflow[item];
-        decode_shot(a, S, shot, lane, deadline);
+        decode_shot<WIN>(a, S, shot, lane, deadline);
     }
 }
 
@@ -1577,20 +1672,64 @@ SlabCaps caps_for_kcap(int kcap, int table_factor) {
 }
 
 cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s) {
-    batch_kernel<<<grid, block, 0, s>>>(a);
+    if (a.carry) batch_kernel<true><<<grid, block, 0, s>>>(a);
+    else batch_kernel<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 int max_block_threads() {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, batch_kernel) != cudaSuccess) return 32;
+    if (cudaFuncGetAttributes(&fa, batch_kernel<false>) != cudaSuccess) return 32;
     return fa.maxThreadsPerBlock > 0 ? fa.maxThreadsPerBlock : 32;
 }
 
 int occupancy_blocks(int block_threads) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel, block_threads, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<false>, block_threads, 0) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
+}
+
+namespace {
+
+// 32 bits of `row` (of `words` words) starting at bit b (bits past the row are 0).
+__device__ __forceinline__ unsigned bits32(const unsigned *row, long long words, long long b) {
+    const long long w = b >> 5;
+    const int sh = (int)(b & 31);
+    const unsigned lo = w < words ? row[w] : 0u;
+    const unsigned hi = (sh && w + 1 < words) ? row[w + 1] : 0u;
+    return sh ? (lo >> sh) | (hi << (32 - sh)) : lo;
+}
+
+__device__ __forceinline__ unsigned low_mask(long long n) {   // bits [0, n) of a word, n clamped to [0, 32]
+    return n <= 0 ? 0u : (n >= 32 ? ~0u : (1u << n) - 1u);
+}
+
+// One thread per (row, window word).
+__global__ void window_assemble_kernel(const unsigned *src, long long src_words, long long bit_begin, int nbits,
+                                       const unsigned *carry, long long carry_words, long long carry_begin,
+                                       int carry_bits, unsigned *dst, long long dst_words, long long num_rows) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= num_rows * dst_words) return;
+    const long long r = i / dst_words, w = i - r * dst_words;
+    const long long b = w * 32;
+    unsigned v = bits32(src + r * src_words, src_words, bit_begin + b) & low_mask(nbits - b);
+    if (carry) v ^= bits32(carry + r * carry_words, carry_words, carry_begin + b) & low_mask(carry_bits - b);
+    dst[i] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_window_assemble(const unsigned *src, long long src_words, long long bit_begin, int nbits,
+                                   const unsigned *carry, long long carry_words, long long carry_begin,
+                                   int carry_bits, unsigned *dst, long long dst_words, long long num_rows,
+                                   cudaStream_t s) {
+    const long long n = num_rows * dst_words;
+    if (n <= 0) return cudaSuccess;
+    const int block = 256;
+    const long long grid = (n + block - 1) / block;
+    window_assemble_kernel<<<(unsigned)grid, block, 0, s>>>(src, src_words, bit_begin, nbits, carry, carry_words,
+                                                             carry_begin, carry_bits, dst, dst_words, num_rows);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s) {

@@ -32,6 +32,7 @@ struct DGraph {
     const unsigned long long *eobs;   // [merged edges]
     const int2 *eend;                 // [merged edges]: (lower detector endpoint, internal weight)
     const int *seid;                  // [row[n]]: merged edge id of every slot
+    const unsigned *commit;           // [words]: detectors of the commit region (sliding windows), or NULL
 };
 
 // Capacities of one warp's slab (per-shot working set).
@@ -69,6 +70,12 @@ struct BatchArgs {
     long long watchdog_ns;       // > 0: shots still running this long after the launch stop (budget status)
     int mode;                    // QEC_MODE_HIERARCHICAL or QEC_MODE_GLOBAL
     int *diag_out;               // [num_shots][QEC_DIAG_FIELDS] per-shot counters, or NULL
+    // sliding-window mode (carry != NULL): the committed observable is XORed
+    // into cobs[shot], the detectors flipped for the next window go to the
+    // shot's carry row (same layout as its syndrome row), statuses only ever
+    // change to a failure, and obs_out / w_out are not written
+    unsigned long long *cobs;
+    unsigned *carry;
 };
 
 long long slab_bytes_for(const SlabCaps &c);
@@ -77,6 +84,13 @@ long long slab_bytes_for(const SlabCaps &c);
 SlabCaps caps_for_kcap(int kcap, int table_factor = 1);
 cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s);
+// Window syndromes from stream syndromes: bit i of window row r is bit
+// (bit_begin + i) of stream row r for i < nbits, XOR bit (carry_begin + i) of
+// carry row r for i < carry_bits (carry may be NULL); rows are padded with zeros.
+cudaError_t launch_window_assemble(const unsigned *src, long long src_words, long long bit_begin, int nbits,
+                                   const unsigned *carry, long long carry_words, long long carry_begin,
+                                   int carry_bits, unsigned *dst, long long dst_words, long long num_rows,
+                                   cudaStream_t s);
 // Order the shots of a mixed batch by graph (graphs in the order given by
 // gorder[0 .. ng)), so that concurrently running warps share one graph; gcnt
 // holds 64 ints of scratch.

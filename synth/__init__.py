@@ -7,6 +7,7 @@ step of the decoding method itself (no edge merging, no distances, no matching).
 """
 
 from .surface import (  # noqa: F401
+    window_graph,
     PhysGraph,
     rotated_surface_code,
     sample_shots,

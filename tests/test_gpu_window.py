@@ -1,0 +1,88 @@
+"""Sliding-window decoding on the GPU (qec_decode_window_batch,
+qec_window_assemble) against the oracle's sliding-window decoding, bit-exact on
+the accumulated committed observable and the status of every stream.  Needs a
+GB300."""
+
+import numpy as np
+import pytest
+
+from oracle.window import sliding_window_decode
+from synth import rotated_surface_code, sample_shots
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_12262_gb300 import build
+    build.build()
+    import paper_2609_12262_gb300 as q
+    q.lib()
+    return q
+
+
+def test_window_assemble_matches_bit_slicing(qd):
+    import torch
+    rng = np.random.default_rng(5)
+    S, sw, ww = 37, 12, 8
+    src = rng.integers(0, 2 ** 32, size=(S, sw), dtype=np.uint64).astype(np.uint32)
+    car = rng.integers(0, 2 ** 32, size=(S, 9), dtype=np.uint64).astype(np.uint32)
+    for begin, nbits, cbeg, cbits in ((0, 200, 0, 0), (37, 201, 5, 90), (64, 256, 31, 256), (300, 83, 200, 1)):
+        dst = torch.empty(S * ww, dtype=torch.int32, device="cuda")
+        t_src = torch.from_numpy(src.view(np.int32).reshape(-1)).cuda()
+        t_car = torch.from_numpy(car.view(np.int32).reshape(-1)).cuda() if cbits else None
+        qd.window_assemble(t_src, sw, begin, nbits, dst, ww, S, carry_rows=t_car, carry_words=9,
+                           carry_bit_begin=cbeg, carry_bits=cbits)
+        torch.cuda.synchronize()
+        got = np.unpackbits(dst.cpu().numpy().view(np.uint8).reshape(S, -1), axis=1, bitorder="little")
+        sb = np.unpackbits(src.view(np.uint8), axis=1, bitorder="little")
+        cb = np.unpackbits(car.view(np.uint8), axis=1, bitorder="little")
+        want = np.zeros((S, ww * 32), np.uint8)
+        n = min(nbits, sb.shape[1] - begin)
+        want[:, :n] = sb[:, begin:begin + n]
+        if cbits:
+            m = min(cbits, cb.shape[1] - cbeg)
+            want[:, :m] ^= cb[:, cbeg:cbeg + m]
+        assert np.array_equal(got, want), (begin, nbits, cbeg, cbits)
+
+
+CASES = [
+    ("d5_R24_W10_C5", dict(d=5, R=24, p=0.01), 10, 5, 400),
+    ("d7_R35_W14_C7", dict(d=7, R=35, p=0.005), 14, 7, 200),
+    ("d5_R20_W8_C3_dense", dict(d=5, R=20, p=0.03), 8, 3, 200),
+    ("d9_R27_W18_C9", dict(d=9, R=27, p=0.004), 18, 9, 100),
+    ("d11_R33_W22_C11_nonuniform", dict(d=11, R=33, p_range=(0.002, 0.006), p_seed=2), 22, 11, 60),
+    ("d5_R12_single_window", dict(d=5, R=12, p=0.01), 30, 10, 200),
+    # long histories: some matched paths span most of a window and need balls
+    # larger than the first tables (the attempt is retried with larger ones);
+    # stream 2801 of this seed has such a window
+    ("d11_R110_W22_C11", dict(d=11, R=110, p=0.003), 22, 11, (3000, 2037, list(range(500)) + [2801])),
+]
+
+
+@pytest.mark.parametrize("name,kw,W,C,S", CASES, ids=[c[0] for c in CASES])
+def test_sliding_window_matches_oracle(qd, name, kw, W, C, S):
+    import torch
+    from paper_2609_12262_gb300.window import SlidingWindow
+    kw = dict(kw)
+    d, R = kw.pop("d"), kw.pop("R")
+    g = rotated_surface_code(d, R, **kw)
+    if isinstance(S, tuple):
+        n, seed, pick = S
+        syn, _ = sample_shots(g, n, seed)
+        syn = np.ascontiguousarray(syn[pick])
+        S = len(pick)
+    else:
+        syn, _ = sample_shots(g, S, 23)
+    dec = SlidingWindow(g, W, C)
+    t = torch.from_numpy(syn.view(np.int32).reshape(-1)).cuda()
+    obs, st = dec.decode(t, S)
+    torch.cuda.synchronize()
+    go, gs = qd.to_uint64(obs), st.cpu().numpy()
+    ro, rs = sliding_window_decode(g, syn, W, C)
+    assert not rs.any()
+    bad = np.nonzero((go != ro) | (gs != rs))[0]
+    assert bad.size == 0, (name, bad[:5].tolist(), go[bad[:3]], ro[bad[:3]])
