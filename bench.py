@@ -38,7 +38,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import mixed_batch, rotated_surface_code, sample_shots  # noqa: E402
+from synth import mixed_batch, rotated_surface_code, rotated_surface_code_circuit, sample_shots  # noqa: E402
 
 METRIC = "shots/s and us per round at d,p (batched vs plain GPU)"
 UNIT = "shots/s"
@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--event-study", action="store_true",
                     help="parallel event count per round, hierarchical vs global, d = 9..49, p = 1e-3..1e-5")
     ap.add_argument("--study-shots", type=int, default=1024)
+    ap.add_argument("--noise", default="phenomenological", choices=["phenomenological", "circuit"],
+                    help="event study noise model: phenomenological graph or circuit-level detector graph")
     ap.add_argument("--study-save", default="", help="directory for the first outputs and diagnostics of every point")
     ap.add_argument("--scaling-save", default="", help="directory for the first outputs of every point")
     return ap.parse_args()
@@ -523,7 +525,7 @@ def event_study(q, args, dev):
     rows = []
     for p in (0.001, 0.0001, 0.00001):
         for d in range(9, 50, 4):
-            pg = rotated_surface_code(d, d, p)
+            pg = rotated_surface_code_circuit(d, d, p) if args.noise == "circuit" else rotated_surface_code(d, d, p)
             seed = args.seed + 7 * d + int(round(-np.log10(p)))
             syn, _ = sample_shots(pg, args.study_shots, seed)
             pc = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)
@@ -538,7 +540,8 @@ def event_study(q, args, dev):
             hw, ho, hs, hd = res["hier"]
             gw, go, gs, gd = res["global"]
             R = float(d)
-            row = {"d": d, "rounds": d, "p": p, "shots": int(syn.shape[0]), "mean_defects": float(pc.mean()),
+            row = {"d": d, "rounds": d, "p": p, "noise": args.noise, "edges": int(pg.num_edges),
+                   "shots": int(syn.shape[0]), "mean_defects": float(pc.mean()),
                    "e_ideal_per_round": float(hd[:, 0].mean() / R), "e_global_per_round": float(gd[:, 0].mean() / R),
                    "e_hier_total_per_round": float(hd[:, 2].mean() / R),
                    "max_e_ideal": int(hd[:, 0].max()), "max_e_global": int(gd[:, 0].max()),

@@ -2,8 +2,10 @@
 
 This package only builds input data: the phenomenological rotated-surface-code
 detector multigraph (one physical edge per elementary fault, each with its own
-probability and integer weight) and syndromes sampled from it.  It contains no
-step of the decoding method itself (no edge merging, no distances, no matching).
+probability and integer weight), the circuit-level detector graph of the same
+code's syndrome-extraction circuit, windows of either, and syndromes sampled
+from them.  It contains no step of the decoding method itself (no edge merging,
+no distances, no matching).
 """
 
 from .surface import (  # noqa: F401
@@ -16,3 +18,4 @@ from .surface import (  # noqa: F401
     pack_defects,
     unpack_defects,
 )
+from .circuit import rotated_surface_code_circuit  # noqa: F401
