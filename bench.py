@@ -74,8 +74,9 @@ def parse():
     ap.add_argument("--event-study", action="store_true",
                     help="parallel event count per round, hierarchical vs global, d = 9..49, p = 1e-3..1e-5")
     ap.add_argument("--study-shots", type=int, default=1024)
-    ap.add_argument("--noise", default="phenomenological", choices=["phenomenological", "circuit"],
-                    help="event study noise model: phenomenological graph or circuit-level detector graph")
+    ap.add_argument("--noise", default="phenomenological", choices=["phenomenological", "circuit", "circuit-physical"],
+                    help="event study noise model: phenomenological graph, or the circuit-level detector graph "
+                         "under the uniform or the physically motivated model")
     ap.add_argument("--study-save", default="", help="directory for the first outputs and diagnostics of every point")
     ap.add_argument("--scaling-save", default="", help="directory for the first outputs of every point")
     return ap.parse_args()
@@ -525,7 +526,10 @@ def event_study(q, args, dev):
     rows = []
     for p in (0.001, 0.0001, 0.00001):
         for d in range(9, 50, 4):
-            pg = rotated_surface_code_circuit(d, d, p) if args.noise == "circuit" else rotated_surface_code(d, d, p)
+            if args.noise == "phenomenological":
+                pg = rotated_surface_code(d, d, p)
+            else:
+                pg = rotated_surface_code_circuit(d, d, p, "physical" if args.noise == "circuit-physical" else "uniform")
             seed = args.seed + 7 * d + int(round(-np.log10(p)))
             syn, _ = sample_shots(pg, args.study_shots, seed)
             pc = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)

@@ -1,41 +1,46 @@
 """Circuit-level detector graphs for the rotated surface code (Z-basis memory).
 
-The paper evaluates on circuit-level detector error models (Methods, noise
-models with uniform and physically motivated rates).  This module builds one
-from scratch for the same code: the syndrome-extraction circuit, every single
-fault of a noise model, and where each fault's Pauli ends up.
+The paper evaluates on circuit-level noise (Methods, "Numerical evaluation"):
+memory experiments of d rounds under two i.i.d. noise models with parameter p.
+This module builds the detector graph of such an experiment from scratch: the
+syndrome-extraction circuit, every single fault of the noise model, and where
+each fault's Pauli ends up.  (The paper's experiments use X-basis memory; this
+is the Z-basis one, its mirror image under exchanging X and Z.)
 
-Circuit (d x d data qubits, one ancilla per stabiliser, layout and check
-types as in surface.py: plaquette (i, j) is Z-type when i + j is even):
+Circuit (d x d data qubits, one ancilla per stabiliser, layout and check types
+as in surface.py: plaquette (i, j) is Z-type when i + j is even), in time steps:
 
-* round t = 0 .. R-1: reset all ancillas; H on X ancillas; four CNOT layers;
-  H on X ancillas; measure all ancillas.  Z ancilla: CNOT data -> ancilla,
-  data order NW, NE, SW, SE; X ancilla: CNOT ancilla -> data, order NW, SW,
-  NE, SE (each CNOT layer touches every qubit at most once, and a fault on an
-  ancilla part-way through propagates to two data qubits lying across the
-  logical operator of its own type, so the circuit distance stays d).
-* data qubits start in |0> and are measured in Z after the last round.
+* step 0: prepare the data qubits in |0>;
+* each round t = 0 .. R-1: prepare all ancillas in |0>; H on X ancillas; four
+  CNOT steps; H on X ancillas; measure all ancillas in Z.  Z ancilla: CNOT
+  data -> ancilla, data order NW, NE, SW, SE; X ancilla: CNOT ancilla -> data,
+  order NW, SW, NE, SE (every step touches each qubit at most once; a fault on
+  an ancilla part-way through spreads to two data qubits lying across the
+  logical of its own type, so the circuit distance stays d);
+* finally every data qubit is measured in Z.
+Every qubit not acted on in a step idles in it.
+
+Noise models (the paper's two):
+* "uniform": a preparation is flipped with probability p; after every one-qubit
+  gate and every idle, X, Y or Z with p/3 each; after every CNOT, one of the 15
+  non-identity two-qubit Paulis with p/15 each; a measurement result flips with
+  probability p.
+* "physical": preparation and measurement flips and CNOT noise as above; after
+  every non-idle one-qubit gate X, Y or Z with p/30 each; idles are noiseless.
+Each depolarising channel is written exactly as a product of independent Pauli
+channels (probabilities chosen so that the product equals the channel), so
+every elementary fault below is independent.
 
 Detectors (Z checks only; X errors are decoded): layer 0 is each Z ancilla's
 first measurement (deterministic), layer t in 1..R-1 compares rounds t-1 and t,
 layer R compares round R-1 with the parity of the final data measurements on
 the check's support.  Observable: the parity of the final data measurements in
-column j = 0 (Z on the left column is the logical Z).
-
-Noise (uniform depolarising, parameter p): after every CNOT a two-qubit
-depolarising channel (one of the 15 non-identity Paulis, each p/15); after
-every reset and every H a one-qubit depolarising channel (X, Y or Z, p/3 each);
-every qubit idle in a CNOT layer gets the same one-qubit channel; every
-measurement result flips with probability p; every data qubit gets a one-qubit
-channel before the first round.  Each channel is written exactly as a product
-of independent Pauli channels (probabilities chosen so that the product equals
-the depolarising channel), so every elementary fault below is independent.
-Each fault is propagated through the rest of the circuit (Pauli frame); its X
-part flips Z-basis measurements, hence detectors and the observable.  Faults with the same (detectors, observable)
-symptom merge into one mechanism with the XOR-combined probability.  Every
-mechanism flips one or two detectors for this circuit (checked); it becomes a
-boundary edge or an edge of the returned PhysGraph, with integer weight
-round(16 ln((1 - p_e) / p_e)).
+column j = 0 (Z on the left column is the logical Z).  Each fault's X part flips
+Z-basis measurements, hence detectors and the observable; faults with the same
+(detectors, observable) symptom merge into one mechanism with the XOR-combined
+probability.  Every mechanism flips one or two detectors for this circuit
+(checked) and becomes a boundary edge or an edge of the returned PhysGraph,
+with integer weight round(16 ln((1 - p_e) / p_e)).
 """
 
 from __future__ import annotations
@@ -74,46 +79,42 @@ XORDER = ("NW", "SW", "NE", "SE")
 
 
 def _circuit(d: int, rounds: int):
-    """The circuit as a list of operations:
-    ('R', q) reset, ('H', q), ('CX', c, t), ('M', q, key) measure, ('IDLE', q),
-    ('TICK',) between layers.  Returns (ops, nq, zchecks, xchecks, zanc, xanc)."""
+    """The circuit as a list of operations in time steps: ('P', q) prepare |0>,
+    ('H', q), ('CX', c, t), ('M', q, key) measure in Z, ('IDLE', q) for every
+    qubit a step does not act on.  Returns (ops, nq, zchecks, xchecks, zanc, xanc)."""
     zc, xc = _checks(d)
     nd = d * d
     zanc = [nd + k for k in range(len(zc))]
     xanc = [nd + len(zc) + k for k in range(len(xc))]
     nq = nd + len(zc) + len(xc)
     ops = []
+
+    def step(acts):
+        busy = set()
+        for op in acts:
+            ops.append(op)
+            busy.update(q for q in op[1:] if isinstance(q, int))
+        for q in range(nq):
+            if q not in busy:
+                ops.append(("IDLE", q))
+
+    step([("P", q) for q in range(nd)])
     for t in range(rounds):
-        for q in zanc + xanc:
-            ops.append(("R", q))
-        for q in xanc:
-            ops.append(("H", q))
-        ops.append(("TICK",))
+        step([("P", q) for q in zanc + xanc])
+        step([("H", q) for q in xanc])
         for layer in range(4):
-            busy = set()
+            acts = []
             for k, c in enumerate(zc):
-                name = ZORDER[layer]
-                if name in c:
-                    ops.append(("CX", c[name], zanc[k]))
-                    busy.update((c[name], zanc[k]))
+                if ZORDER[layer] in c:
+                    acts.append(("CX", c[ZORDER[layer]], zanc[k]))
             for k, c in enumerate(xc):
-                name = XORDER[layer]
-                if name in c:
-                    ops.append(("CX", xanc[k], c[name]))
-                    busy.update((c[name], xanc[k]))
-            for q in range(nq):
-                if q not in busy:
-                    ops.append(("IDLE", q))
-            ops.append(("TICK",))
-        for q in xanc:
-            ops.append(("H", q))
-        for k, q in enumerate(zanc):
-            ops.append(("M", q, ("z", t, k)))
-        for k, q in enumerate(xanc):
-            ops.append(("M", q, ("x", t, k)))
-        ops.append(("TICK",))
-    for q in range(nd):
-        ops.append(("M", q, ("data", q)))
+                if XORDER[layer] in c:
+                    acts.append(("CX", xanc[k], c[XORDER[layer]]))
+            step(acts)
+        step([("H", q) for q in xanc])
+        step([("M", q, ("z", t, k)) for k, q in enumerate(zanc)] +
+             [("M", q, ("x", t, k)) for k, q in enumerate(xanc)])
+    ops.extend(("M", q, ("data", q)) for q in range(nd))
     return ops, nq, zc, xc, zanc, xanc
 
 
@@ -144,8 +145,9 @@ def backward_sensitivity(ops, nq, key_effect, visit):
     point; before stepping back over ops[i], call visit(i, op, FX, FZ) with the
     sensitivity of the point just after ops[i].  Stepping back applies the
     inverse of each operation's action on an error frame: a CNOT copies X from
-    control to target and Z from target to control, H exchanges X and Z, a reset
-    absorbs every error, a Z measurement reports an X error and keeps it."""
+    control to target and Z from target to control, H exchanges X and Z, a
+    preparation absorbs every earlier error, a Z measurement reports an X error
+    and keeps it."""
     empty = (frozenset(), 0)
     FX = [empty] * nq
     FZ = [empty] * nq
@@ -160,7 +162,7 @@ def backward_sensitivity(ops, nq, key_effect, visit):
         elif kind == "H":
             q = op[1]
             FX[q], FZ[q] = FZ[q], FX[q]
-        elif kind == "R":
+        elif kind == "P":
             FX[op[1]] = empty
             FZ[op[1]] = empty
         elif kind == "M":
@@ -169,18 +171,23 @@ def backward_sensitivity(ops, nq, key_effect, visit):
     return FX, FZ
 
 
-def rotated_surface_code_circuit(d: int, rounds: int | None = None, p: float = 0.001, *, p_cx=None,
-                                 p_1q=None, p_idle=None, p_meas=None, p_data=None) -> PhysGraph:
+def rotated_surface_code_circuit(d: int, rounds: int | None = None, p: float = 0.001, noise: str = "uniform",
+                                 *, p_cx=None, p_1q=None, p_idle=None, p_meas=None, p_prep=None) -> PhysGraph:
     """Circuit-level detector graph of a d-round (default) Z-basis memory
-    experiment (see the module docstring).  Every noise component has rate p
-    unless given: p_cx (two-qubit channel after a CNOT), p_1q (after reset and
-    H), p_idle (idle qubit in a CNOT layer), p_meas (measurement flip), p_data
-    (data qubits before the first round)."""
+    experiment under the paper's "uniform" or "physical" noise model with
+    parameter p (see the module docstring).  Keyword rates override single
+    components: p_cx (two-qubit depolarising after a CNOT), p_1q (one-qubit
+    depolarising after H), p_idle (after an idle), p_meas (measurement flip),
+    p_prep (preparation flip)."""
     if d < 3 or d % 2 == 0:
         raise ValueError("d must be odd and >= 3")
+    if noise not in ("uniform", "physical"):
+        raise ValueError("noise must be 'uniform' or 'physical'")
     R = d if rounds is None else int(rounds)
-    rate = {k: (p if v is None else float(v)) for k, v in
-            (("cx", p_cx), ("1q", p_1q), ("idle", p_idle), ("meas", p_meas), ("data", p_data))}
+    base = {"cx": p, "1q": p if noise == "uniform" else p / 10, "idle": p if noise == "uniform" else 0.0,
+            "meas": p, "prep": p}
+    rate = {k: (base[k] if v is None else float(v)) for k, v in
+            (("cx", p_cx), ("1q", p_1q), ("idle", p_idle), ("meas", p_meas), ("prep", p_prep))}
     ops, nq, zc, xc, zanc, xanc = _circuit(d, R)
     nz = len(zc)
     nd = d * d
@@ -204,7 +211,9 @@ def rotated_surface_code_circuit(d: int, rounds: int | None = None, p: float = 0
 
     def visit(i, op, FX, FZ):
         kind = op[0]
-        if kind in ("R", "H"):
+        if kind == "P":
+            add(rate["prep"], FX[op[1]])   # the prepared |0> flipped: an X error
+        elif kind == "H":
             one_qubit(FX, FZ, op[1], rate["1q"])
         elif kind == "IDLE":
             one_qubit(FX, FZ, op[1], rate["idle"])
@@ -227,9 +236,7 @@ def rotated_surface_code_circuit(d: int, rounds: int | None = None, p: float = 0
         elif kind == "M" and op[2][0] in ("z", "data"):
             add(rate["meas"], key_effect(op[2]))
 
-    FX, FZ = backward_sensitivity(ops, nq, key_effect, visit)
-    for q in range(nd):                # data qubits before the first round
-        one_qubit(FX, FZ, q, rate["data"])
+    backward_sensitivity(ops, nq, key_effect, visit)
     us, vs, obs, pe, kind = [], [], [], [], []
     for (det, ob), prob in sorted(mech.items(), key=lambda kv: (sorted(kv[0][0]), kv[0][1])):
         det = sorted(det)

@@ -7,8 +7,9 @@ things other than its own backward propagation:
   distance) is d with the chosen CNOT orders, and smaller when the X-ancilla
   order puts its hook along the logical operator;
 * measurement noise alone gives exactly the time edges (one per check and
-  round) and the final data-measurement edges; data noise before the first
-  round alone gives the phenomenological graph's first-layer space edges;
+  round) and the final data-measurement edges; preparation noise alone gives
+  the phenomenological graph's first-layer space edges (data qubits) and the
+  time edges (Z ancillas), each with the preparation flip probability;
 * decoding circuit-level syndromes: hierarchical == global (Theorem 1)."""
 
 from collections import deque
@@ -39,7 +40,7 @@ def forward_effect(d, R, ops, nq, zc, start, xs, zs):
         elif op[0] == "H":
             q = op[1]
             x[q], z[q] = z[q], x[q]
-        elif op[0] == "R":
+        elif op[0] == "P":
             x[op[1]] = 0
             z[op[1]] = 0
         elif op[0] == "M" and x[op[1]]:
@@ -122,8 +123,9 @@ def circuit_distance(g):
 
 
 @pytest.mark.parametrize("d", [3, 5, 7])
-def test_circuit_distance_is_d(d):
-    assert circuit_distance(rotated_surface_code_circuit(d, d, 0.001)) == d
+@pytest.mark.parametrize("noise", ["uniform", "physical"])
+def test_circuit_distance_is_d(d, noise):
+    assert circuit_distance(rotated_surface_code_circuit(d, d, 0.001, noise)) == d
 
 
 def test_hook_along_the_logical_halves_the_distance(monkeypatch):
@@ -133,7 +135,7 @@ def test_hook_along_the_logical_halves_the_distance(monkeypatch):
 
 def test_measurement_noise_alone_gives_time_edges():
     d, R, p = 5, 6, 0.002
-    g = rotated_surface_code_circuit(d, R, p, p_cx=0, p_1q=0, p_idle=0, p_data=0)
+    g = rotated_surface_code_circuit(d, R, p, p_cx=0, p_1q=0, p_idle=0, p_prep=0)
     nz = g.nz
     time_edges = {(t * nz + k, (t + 1) * nz + k) for t in range(R) for k in range(nz)}
     got = {(int(u), int(v)) for u, v in zip(g.u, g.v)}
@@ -145,16 +147,20 @@ def test_measurement_noise_alone_gives_time_edges():
             assert u // nz == R and (v < 0 or v // nz == R)
 
 
-def test_data_noise_alone_gives_the_first_layer_space_edges():
-    d, p = 5, 0.003
-    g = rotated_surface_code_circuit(d, 4, p, p_cx=0, p_1q=0, p_idle=0, p_meas=0)
-    ph = rotated_surface_code(d, 4, 0.01)
+def test_preparation_noise_alone():
+    d, R, p = 5, 4, 0.003
+    g = rotated_surface_code_circuit(d, R, p, p_cx=0, p_1q=0, p_idle=0, p_meas=0)
+    nz = g.nz
+    ph = rotated_surface_code(d, R, 0.01)
     first = [(int(u), int(v), int(o)) for u, v, o, k in zip(ph.u, ph.v, ph.obs, ph.kind)
-             if k == 0 and u < ph.nz]
+             if k == 0 and u < nz]
     want = {}
-    for e in first:   # each data qubit: X or Y with probability 2p/3; parallel copies combine
+    for e in first:   # each data qubit prepared flipped with probability p; parallel copies combine
         q = want.get(e, 0.0)
-        want[e] = q * (1 - 2 * p / 3) + (2 * p / 3) * (1 - q)
+        want[e] = q * (1 - p) + p * (1 - q)
+    for t in range(R):   # a flipped Z-ancilla preparation flips that round's measurement
+        for k in range(nz):
+            want[(t * nz + k, (t + 1) * nz + k, 0)] = p
     got = {(int(u), int(v), int(o)): float(pe) for u, v, o, pe in zip(g.u, g.v, g.obs, g.p)}
     assert set(got) == set(want)
     for e in want:

@@ -24,13 +24,15 @@ def qd():
     return q
 
 
-CASES = [(3, 0.005, 4000), (5, 0.003, 2000), (7, 0.002, 1000), (9, 0.001, 800), (5, 0.008, 800), (13, 0.003, 150)]
+CASES = [(3, 0.005, "uniform", 4000), (5, 0.003, "uniform", 2000), (7, 0.002, "uniform", 1000),
+         (9, 0.001, "uniform", 800), (5, 0.008, "uniform", 800), (13, 0.003, "uniform", 150),
+         (5, 0.006, "physical", 2000), (9, 0.002, "physical", 600)]
 
 
-@pytest.mark.parametrize("d,p,shots", CASES, ids=["d%d_p%g" % (c[0], c[1]) for c in CASES])
-def test_circuit_level_matches_oracle(qd, d, p, shots):
+@pytest.mark.parametrize("d,p,noise,shots", CASES, ids=["%s_d%d_p%g" % (c[2], c[0], c[1]) for c in CASES])
+def test_circuit_level_matches_oracle(qd, d, p, noise, shots):
     import torch
-    g = rotated_surface_code_circuit(d, d, p)
+    g = rotated_surface_code_circuit(d, d, p, noise)
     qg = qd.Graph.from_phys(g)
     syn, _ = sample_shots(g, shots, 31)
     t = torch.from_numpy(syn.view(np.int32).reshape(-1)).cuda()
