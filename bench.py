@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--event-study", action="store_true",
                     help="parallel event count per round, hierarchical vs global, d = 9..49, p = 1e-3..1e-5")
     ap.add_argument("--study-shots", type=int, default=1024)
+    ap.add_argument("--study-d", type=int, nargs="*", default=None, help="event study: only these distances")
+    ap.add_argument("--study-p", type=float, nargs="*", default=None, help="event study: only these error rates")
     ap.add_argument("--noise", default="phenomenological", choices=["phenomenological", "circuit", "circuit-physical"],
                     help="event study noise model: phenomenological graph, or the circuit-level detector graph "
                          "under the uniform or the physically motivated model")
@@ -525,7 +527,11 @@ def event_study(q, args, dev):
     import torch
     rows = []
     for p in (0.001, 0.0001, 0.00001):
+        if args.study_p and p not in args.study_p:
+            continue
         for d in range(9, 50, 4):
+            if args.study_d and d not in args.study_d:
+                continue
             if args.noise == "phenomenological":
                 pg = rotated_surface_code(d, d, p)
             else:
@@ -538,7 +544,20 @@ def event_study(q, args, dev):
             t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
             res = {}
             for mode in ("hier", "global"):
-                o, w, st, dg = q.decode_batch_ex([g], t, mode=mode)
+                if mode == "global" and pc.mean() > 500:
+                    # every region explores from t = 0: tables twice as large, and
+                    # launches of 256 shots so that each ends well inside the watchdog
+                    q.set_tuning(kcap=2 * max(64, int(pc.max() * 1.1) + 8), warps_per_block=1, blocks_per_sm=2)
+                    parts = []
+                    for c0 in range(0, syn.shape[0], 256):
+                        n = min(256, syn.shape[0] - c0)
+                        sub = t[c0 * pg.words:(c0 + n) * pg.words]
+                        parts.append(q.decode_batch_ex([g], sub, num_shots=n, mode=mode))
+                    torch.cuda.synchronize()
+                    o, w, st, dg = (torch.cat([x[i] for x in parts]) for i in range(4))
+                    q.set_tuning(kcap=max(64, int(pc.max() * 1.1) + 8), warps_per_block=-1, blocks_per_sm=-1)
+                else:
+                    o, w, st, dg = q.decode_batch_ex([g], t, mode=mode)
                 torch.cuda.synchronize()
                 res[mode] = (w.cpu().numpy(), q.to_uint64(o), st.cpu().numpy(), dg.cpu().numpy())
             hw, ho, hs, hd = res["hier"]
