@@ -97,12 +97,23 @@ PROFILE = os.path.join(ROOT, "profiles", "batch_kernel_mixed_d7-21_p003.md")
 KERNEL_SOURCES = ["decoder.cu", "qec_internal.h", "capi.cpp"]
 
 
+_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)
+
+
+def _code_only(text):
+    """Source text without comments and with whitespace collapsed (string
+    literals kept), so that editing a comment does not count as a change."""
+    text = _TOKENS.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text)
+    return " ".join(text.split())
+
+
 def kernel_sha256():
+    """SHA-256 over the code (comments and whitespace aside) of the kernel sources."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2609_12262_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2609_12262_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

@@ -6,26 +6,33 @@
 //      vector loads and compacted by a warp prefix sum (input D of the paper's
 //      "Decoding task"; Alg. 1 input).
 //   2. flooder: every detection event s owns an explored ball {x : dist(s,x) <=
-//      R_s} with exact graph distances (hash table keyed by (vertex, event)).
-//      A ball is grown band by band (R -> R + band, band >= largest weight) by
-//      warp-parallel label-correcting relaxation from the previous band; each
-//      new vertex is checked against the other events' balls at itself and at
-//      its neighbours, which records the exact distance of every pair of
-//      events whose balls touch.  The graph-fill region of s (SI S1) is the
-//      ball of radius Rad(s) <= R_s, so two regions are found touching exactly
-//      when their pair distance equals Rad(a) + Rad(b) (ARRIVE = a band
-//      extension, COLLIDE = a tight pair, boundary COLLIDE = Rad(s) reaching
-//      the nearest boundary, IMPLODE = an inner blossom's dual reaching 0).
-//   3. Algorithm 1, level 1: balls of radius b_1/2 give every pair within b_1
-//      and every boundary contact; union-find links, diameter <= d_1 and the
-//      parity condition decide the level-1 processing clusters.
+//      R_s} with exact graph distances (hash table keyed by (vertex, event)),
+//      explored once its region starts growing and kept at R_s >= Rad(s) + L
+//      (L above the largest weight).  A ball is grown band by band (band >=
+//      largest weight) by warp-parallel label-correcting relaxation from the
+//      previous band; each new entry is checked against the other events'
+//      balls holding the same vertex, and against events sitting on it, which
+//      records the exact distance of every pair of events whose balls touch.
+//      The graph-fill region of s (SI S1) is the ball of radius Rad(s) <= R_s,
+//      so two regions are found touching exactly when their pair distance
+//      equals Rad(a) + Rad(b) (ARRIVE = a band extension, COLLIDE = a tight
+//      pair, boundary COLLIDE = Rad(s) reaching the nearest boundary, IMPLODE =
+//      an inner blossom's dual reaching 0).
+//   3. Algorithm 1, level 1: each event's neighbourhood within b_1 (paths of
+//      one or two edges when three smallest weights exceed b_1, else a bounded
+//      search) gives every pair within b_1 and every boundary contact; min-label
+//      components, the diameter <= d_1 test and the parity condition decide the
+//      level-1 processing clusters.
 //   4. Algorithm 2: level-1 clusters are solved independently (closed form for
 //      the isolated pair and boundary singleton, the event loop otherwise), then
 //      every remaining event runs from t = 0 with the stopped level-1
 //      configurations present as frozen regions (hierarchical execution rule).
+//      Global mode runs every event in one execution instead.
 //   5. Tracing: blossoms are expanded into matched event pairs and boundary
 //      matches; the weight is the sum of the tight pair / boundary distances and
-//      the observable mask the XOR of the canonical paths' masks.
+//      the observable mask the XOR of the canonical paths' masks.  The
+//      sliding-window instantiation (batch_kernel<true>) also walks every path
+//      and commits the edges that touch the window's commit region.
 //
 // Simultaneous events are applied in the canonical order (t, kind, lo, hi) with
 // kind EXTEND < IMPLODE < COLLIDE < BOUNDARY and lo, hi the ranks of the events
