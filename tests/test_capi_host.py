@@ -108,3 +108,18 @@ def test_decode_rejects_bad_args(L):
     assert L.qec_decode_batch(arr, 1, None, None, None, -1, None, None, None, None) == q.QEC_EINVAL
     assert L.qec_decode_batch(arr, 1, None, None, None, 0, None, None, None, None) == q.QEC_OK
     assert L.qec_decode_batch(arr, 33, None, None, None, 5, None, None, None, None) == q.QEC_EINVAL
+
+
+def test_window_assemble_validates_before_touching_memory(L):
+    """Argument errors are reported before any device access (the pointers
+    below are never dereferenced)."""
+    fake = C.c_void_p(16)
+    rc = L.qec_window_assemble(fake, 8, 0, 300, None, 0, 0, 0, fake, 8, 4, None)   # 300 bits > 8 words
+    assert rc == q.QEC_ERANGE
+    rc = L.qec_window_assemble(fake, 8, -1, 10, None, 0, 0, 0, fake, 8, 4, None)
+    assert rc == q.QEC_EINVAL
+    rc = L.qec_window_assemble(fake, 8, 0, 10, fake, 0, 0, 10, fake, 8, 4, None)   # carry rows of 0 words
+    assert rc == q.QEC_EINVAL
+    rc = L.qec_window_assemble(None, 8, 0, 10, None, 0, 0, 0, fake, 8, 4, None)
+    assert rc == q.QEC_EINVAL
+    assert L.qec_window_assemble(fake, 8, 0, 10, None, 0, 0, 0, fake, 8, 0, None) == q.QEC_OK   # no rows

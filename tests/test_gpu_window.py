@@ -86,3 +86,24 @@ def test_sliding_window_matches_oracle(qd, name, kw, W, C, S):
     assert not rs.any()
     bad = np.nonzero((go != ro) | (gs != rs))[0]
     assert bad.size == 0, (name, bad[:5].tolist(), go[bad[:3]], ro[bad[:3]])
+
+
+def test_window_decode_needs_a_commit_region(qd):
+    import torch
+    g = qd.Graph.from_phys(rotated_surface_code(5, 5, 0.01))
+    S = 4
+    rows = torch.zeros(S * g.words, dtype=torch.int32, device="cuda")
+    obs = torch.zeros(S, dtype=torch.int64, device="cuda")
+    st = torch.zeros(S, dtype=torch.int32, device="cuda")
+    carry = torch.empty_like(rows)
+    with pytest.raises(qd.QecError):
+        qd.decode_window_batch([g], rows, obs, carry, st, num_shots=S)
+    bits = np.zeros(g.words, np.uint32)
+    bits[0] = 0xfff
+    g.set_commit_region(bits)
+    qd.decode_window_batch([g], rows, obs, carry, st, num_shots=S)   # empty syndromes: nothing committed
+    torch.cuda.synchronize()
+    assert not obs.any() and not st.any() and not carry.any()
+    g.set_commit_region(None)
+    with pytest.raises(qd.QecError):
+        qd.decode_window_batch([g], rows, obs, carry, st, num_shots=S)
