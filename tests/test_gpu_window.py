@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle.window import sliding_window_decode
-from synth import rotated_surface_code, sample_shots
+from synth import rotated_surface_code, rotated_surface_code_circuit, sample_shots
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +60,9 @@ CASES = [
     # larger than the first tables (the attempt is retried with larger ones);
     # stream 2801 of this seed has such a window
     ("d11_R110_W22_C11", dict(d=11, R=110, p=0.003), 22, 11, (3000, 2037, list(range(500)) + [2801])),
+    # circuit-level histories: diagonal space-time edges cross the window boundaries
+    ("circuit_d5_R20_W10_C5", dict(d=5, R=20, p=0.003, circuit=True), 10, 5, 300),
+    ("circuit_d7_R21_W14_C7", dict(d=7, R=21, p=0.002, circuit=True), 14, 7, 150),
 ]
 
 
@@ -69,7 +72,7 @@ def test_sliding_window_matches_oracle(qd, name, kw, W, C, S):
     from paper_2609_12262_gb300.window import SlidingWindow
     kw = dict(kw)
     d, R = kw.pop("d"), kw.pop("R")
-    g = rotated_surface_code(d, R, **kw)
+    g = rotated_surface_code_circuit(d, R, kw["p"]) if kw.pop("circuit", False) else rotated_surface_code(d, R, **kw)
     if isinstance(S, tuple):
         n, seed, pick = S
         syn, _ = sample_shots(g, n, seed)

@@ -10,7 +10,7 @@ import pytest
 
 from oracle import OracleGraph
 from oracle.window import sliding_window_decode, windows
-from synth import rotated_surface_code, sample_shots, unpack_defects, window_graph
+from synth import rotated_surface_code, rotated_surface_code_circuit, sample_shots, unpack_defects, window_graph
 
 
 def test_window_plan_tiles_the_layers():
@@ -44,10 +44,11 @@ def test_single_window_is_global(d, R, p, shots):
     assert np.array_equal(st, S) and np.array_equal(obs, O)
 
 
-@pytest.mark.parametrize("d,R,p,W,C,shots", [(5, 24, 0.01, 10, 5, 60), (5, 20, 0.03, 8, 3, 50),
-                                              (7, 21, 0.005, 14, 7, 30), (5, 16, 0.02, 6, 6, 40)])
-def test_committed_edges_correct_the_history(d, R, p, W, C, shots):
-    g = rotated_surface_code(d, R, p)
+@pytest.mark.parametrize("d,R,p,W,C,shots,circuit", [(5, 24, 0.01, 10, 5, 60, False), (5, 20, 0.03, 8, 3, 50, False),
+                                                      (7, 21, 0.005, 14, 7, 30, False), (5, 16, 0.02, 6, 6, 40, False),
+                                                      (5, 20, 0.003, 10, 5, 40, True), (5, 15, 0.006, 6, 3, 30, True)])
+def test_committed_edges_correct_the_history(d, R, p, W, C, shots, circuit):
+    g = rotated_surface_code_circuit(d, R, p) if circuit else rotated_surface_code(d, R, p)
     syn, _ = sample_shots(g, shots, 8)
     obs, st, edges = sliding_window_decode(g, syn, W, C, return_edges=True)
     assert not st.any()
