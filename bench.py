@@ -255,6 +255,38 @@ def cpu_oracle_rate(graphs, gid, offs, syn, seconds, workers=None):
     return done / t_used, done, t_used, ncores
 
 
+def cpu_model():
+    """The host CPU's model name (Linux /proc/cpuinfo, else the platform string)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_oracle_one_core(graphs, gid, offs, syn, seconds):
+    """The CPU oracle in this process alone (one core) on a bounded sample."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle_pool import oracle_decode
+    rng = np.random.default_rng(6)
+    order = rng.permutation(gid.shape[0])
+    done, t_used, n = 0, 0.0, 16
+    while t_used < seconds and done < order.size:
+        sel = order[done:done + n]
+        rows = [syn[offs[s]:offs[s] + graphs[gid[s]].words] for s in sel]
+        t0 = time.perf_counter()
+        oracle_decode(graphs, gid[sel], rows, mode="hier", workers=1)
+        t_used += time.perf_counter() - t0
+        done += sel.size
+        n = min(n * 2, 4096)
+    return done / t_used, done
+
+
 def serving_run(q, args, dev):
     """Poisson arrivals into a qec_stream; latency = result time - scheduled arrival."""
     import torch
@@ -795,8 +827,10 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, secs, cores = cpu_oracle_rate(graphs, gid, offs, syn, args.cpu_seconds)
+        rate1, n1 = cpu_oracle_one_core(graphs, gid, offs, syn, min(4.0, args.cpu_seconds / 3))
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d uniformly drawn shots of the same batch, %.1f s wall on %d processes" % (n, secs, cores)}
+               "sample": "%d uniformly drawn shots of the same batch, %.1f s wall on %d processes" % (n, secs, cores),
+               "cpu_model": cpu_model(), "one_core": {"value": rate1, "unit": UNIT, "sample": "%d shots" % n1}}
 
     if rank == 0:
         line = {
