@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving run length (0 = skip); 5 s = 10^6 windows at 200k/s")
     ap.add_argument("--serve-rate", type=float, default=200000.0, help="Poisson arrival rate, windows/s")
+    ap.add_argument("--serve-oracle", type=int, default=3000, help="served windows checked against the oracle")
     ap.add_argument("--scaling", action="store_true",
                     help="scaling study: d in {25,31,41,51} x p in {.001,.003,.005}, us per round vs d")
     ap.add_argument("--scaling-shots", type=int, default=10000)
@@ -243,16 +244,29 @@ def cpu_oracle_rate(graphs, gid, offs, syn, seconds, workers=None):
     rng = np.random.default_rng(5)
     order = rng.permutation(gid.shape[0])
     done, t_used, n = 0, 0.0, 8 * ncores
+    res = []
     while t_used < seconds and done < order.size:
         sel = order[done:done + n]
         rows = [syn[offs[s]:offs[s] + graphs[gid[s]].words] for s in sel]
         t0 = time.perf_counter()
-        pool.decode(gid[sel], rows, mode="hier")
+        w, o, st = pool.decode(gid[sel], rows, mode="hier")
         t_used += time.perf_counter() - t0
+        res.append((sel, w, o, st))
         done += sel.size
         n = min(n * 2, 16384)
     pool.close()
-    return done / t_used, done, t_used, ncores
+    idx = np.concatenate([r[0] for r in res])
+    ref = tuple(np.concatenate([r[i] for r in res]) for i in (1, 2, 3))
+    return done / t_used, done, t_used, ncores, (idx, ref)
+
+
+def parity_vs_oracle(checked, gpu_w, gpu_o, gpu_s):
+    """Element-by-element comparison of GPU outputs with the oracle's results
+    (idx: shot indices, ref: oracle weight, observable, status)."""
+    idx, (rw, ro, rs) = checked
+    bad = (gpu_w[idx] != rw) | (gpu_o[idx] != ro) | (gpu_s[idx] != rs)
+    return {"checked": int(idx.size), "mismatches": int(np.count_nonzero(bad)),
+            "against": "oracle (weight, observable, status per shot)"}
 
 
 def cpu_model():
@@ -335,11 +349,25 @@ def serving_run(q, args, dev):
     torch.cuda.synchronize()
     bw, bo, bs = w.cpu().numpy(), q.to_uint64(o), s_.cpu().numpy()
     mism = int(np.count_nonzero(ok & ((bw != got_w) | (bo != got_o) | (bs != got_s))))
+    # served results against the oracle, on a uniform sample of the windows
+    oracle_check = None
+    if args.serve_oracle > 0 and ok.any():
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from oracle_pool import OraclePool
+        pick = np.random.default_rng(args.seed + 79).choice(np.nonzero(ok)[0], size=min(args.serve_oracle, int(ok.sum())),
+                                                            replace=False)
+        pool = OraclePool(graphs, os.cpu_count() or 1)
+        rows = [syn[offs[k]:offs[k] + graphs[gid[k]].words] for k in pick]
+        rw, ro, rs = pool.decode(gid[pick], rows, mode="hier")
+        pool.close()
+        oracle_check = {"checked": int(pick.size), "mismatches": int(np.count_nonzero(
+            (rw != got_w[pick]) | (ro != got_o[pick]) | (rs != got_s[pick]))),
+            "sample": "uniformly drawn served windows, compared on weight, observable and status"}
     return {"windows": N, "completed": int(ok.sum()), "offered_rate": args.serve_rate,
             "sustained": float(ok.sum() / span), "unit": "windows/s",
             "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
             "p999_us": float(np.percentile(lat_us, 99.9)), "max_us": float(lat_us.max()),
-            "distances": sds, "p": args.p, "mismatch_vs_batch": mism,
+            "distances": sds, "p": args.p, "mismatch_vs_batch": mism, "oracle": oracle_check,
             "latency": "result available on the host minus the scheduled Poisson arrival"}
 
 
@@ -443,7 +471,7 @@ def config_study(q, args, dev):
         if not args.no_cpu_baseline:
             gid = np.zeros(S, np.int32)
             offs = np.arange(S, dtype=np.int64) * pg.words
-            rate, n, secs, cores = cpu_oracle_rate([pg], gid, offs, syn.reshape(-1), args.cpu_seconds)
+            rate, n, secs, cores, _ = cpu_oracle_rate([pg], gid, offs, syn.reshape(-1), args.cpu_seconds)
             row["cpu_baseline"] = {"value": rate, "unit": "shots/s", "cores": cores, "kind": "oracle",
                                    "sample": "%d shots of this configuration in %.1f s" % (n, secs)}
         rows.append(row)
@@ -466,8 +494,8 @@ def stream_study(q, args, dev):
         pg = rotated_surface_code(d, R, 0.003)
         syn, _ = sample_shots(pg, S, args.seed + d)
         t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
-        dec = SlidingWindow(pg, 2 * d, d)
         whole = q.Graph.from_phys(pg)
+        dec = SlidingWindow(whole, pg.nz, 2 * d, d)
         q.set_tuning(kcap=max(64, int(np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1).max()) + 8),
                      blocks_per_sm=-1, warps_per_block=-1)
         dec.decode(t, S)
@@ -730,6 +758,7 @@ def main():
     torch.cuda.synchronize()
     st = out[2].cpu().numpy()
     bad_status = int(np.count_nonzero(st != 0))
+    out[0].zero_(); out[1].zero_(); out[2].fill_(-1)
 
     def barrier():
         if dist is not None:
@@ -750,6 +779,8 @@ def main():
         barrier()
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
+    # outputs of the last timed step (compared with the oracle's below)
+    timed_out = (out[1].cpu().numpy(), q.to_uint64(out[0]), out[2].cpu().numpy())
     if dist is not None:
         from paper_2609_12262_gb300.replicas import max_over_ranks
         total_ms = max_over_ranks(total_ms, dev)
@@ -825,12 +856,14 @@ def main():
         serving = serving_run(q, args, dev)
 
     cpu = None
+    parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, n, secs, cores = cpu_oracle_rate(graphs, gid, offs, syn, args.cpu_seconds)
+        rate, n, secs, cores, checked = cpu_oracle_rate(graphs, gid, offs, syn, args.cpu_seconds)
         rate1, n1 = cpu_oracle_one_core(graphs, gid, offs, syn, min(4.0, args.cpu_seconds / 3))
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d uniformly drawn shots of the same batch, %.1f s wall on %d processes" % (n, secs, cores),
                "cpu_model": cpu_model(), "one_core": {"value": rate1, "unit": UNIT, "sample": "%d shots" % n1}}
+        parity = parity_vs_oracle(checked, timed_out[0], timed_out[1], timed_out[2])
 
     if rank == 0:
         line = {
@@ -861,6 +894,7 @@ def main():
             "e2e": e2e,
             "serving": serving,
             "cpu_baseline": cpu,
+            "parity": parity,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

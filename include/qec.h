@@ -102,6 +102,14 @@ typedef struct {
     int64_t b_k[8];            /* Alg. 3 buffers b_k^V, internal units */
     int32_t device;            /* CUDA device holding the graph */
     int32_t has_internal_obs;  /* some detector-detector edge carries an observable */
+    int32_t components;        /* connected components of the detector graph */
+    int32_t upper_single_cluster; /* 1: every detection event left after level 1
+                                  * forms one processing cluster (one component,
+                                  * b_2 >= distance_bound, and a later d_k covers
+                                  * it); the hierarchical execution is then level 1
+                                  * plus one top-level cluster exactly */
+    int64_t distance_bound;    /* upper bound on the distance between two connected
+                                * detectors, internal units */
 } qec_graph_info;
 
 /* Algorithm 3 (Methods, "Finite-size parameter schedule") for a graph whose
@@ -125,6 +133,20 @@ int qec_schedule(int32_t wmax_internal, const qec_params *params, int64_t *d_k, 
 int qec_graph_create(const qec_graph_desc *desc, qec_graph **out);
 int qec_graph_destroy(qec_graph *g);
 int qec_graph_get_info(const qec_graph *g, qec_graph_info *out);
+
+/* Create the graph of one sliding window of a stream graph (the windowing rule
+ * stated with qec_decode_window_batch below): the induced subgraph of `stream`
+ * on its detectors [first_detector, first_detector + num_detectors), with those
+ * detectors renumbered from 0 in the same order.  It holds every merged edge of
+ * `stream` whose detector endpoints all lie in the range (boundary edges of
+ * those detectors included) with its weight and observable mask; edges that
+ * leave the range are left out.  params: host or NULL (NULL = the parameters
+ * `stream` was created with).  The window is a graph of its own: on the
+ * current device, owned by the library until qec_graph_destroy.  Errors:
+ * QEC_EINVAL (NULL stream or out, bad params), QEC_ERANGE (range outside the
+ * stream's detectors), and those of qec_graph_create.  *out is NULL on failure. */
+int qec_graph_create_window(const qec_graph *stream, int32_t first_detector, int32_t num_detectors,
+                            const qec_params *params, qec_graph **out);
 
 /* Copy the merged edge list to host arrays of qec_graph_info.num_merged_edges
  * entries (u, v with -1 = boundary, internal weight = 2w, obs).  Any pointer may
@@ -176,8 +198,11 @@ enum {
  * top-level run with N events, E_top(t1) of them at times <= t1, gives
  * E_ideal = max(E1, E_top(t1)) + N - E_top(t1) (E1 when no event is left after
  * level 1), which is the paper's recursion when every event above level 1
- * forms one processing cluster (true whenever b_2 is at least the graph's
- * diameter, as for the rotated surface codes of the benchmarks).  In global
+ * forms one processing cluster: qec_graph_info.upper_single_cluster = 1, true
+ * for every rotated-surface-code graph here (phenomenological and circuit
+ * level) under the default and the tested custom schedules.  On a graph where it
+ * is 0 the hierarchical run still returns the matching of Theorem 1, but the
+ * counts are those of level 1 plus one run of all remaining events.  In global
  * mode E_ideal is the run's whole event count.  Times are in internal units
  * (twice the integer weights).  Shots whose status is not QEC_SHOT_OK and
  * shots without detection events get all zeros. */
@@ -289,13 +314,17 @@ int qec_get_tuning(qec_tuning *t);
  * holds until the process exits; it calls no cudaMalloc, cudaFree or other
  * allocating routine.
  *
- * Arguments, layouts and outputs are those of qec_decode_batch.  Limits:
+ * Arguments, layouts and outputs are those of qec_decode_batch, and the band
+ * width and event budget set by qec_set_tuning apply as there (the other
+ * knobs do not: the launch shape and slab size are fixed).  Limits:
  * num_shots <= QEC_STATIC_MAX_SHOTS (else QEC_ERANGE, nothing launched); a
  * shot with more than QEC_STATIC_MAX_EVENTS detection events ends with status
  * QEC_SHOT_CAPACITY, and so does every shot of a graph whose rows exceed
  * QEC_STREAM_MAX_WORDS words.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the array and zeroes its
+ * address (cudaGetSymbolAddress) with that device current and enqueues one fill
+ * of the array on `stream`; it returns QEC_EINVAL if `stream` is capturing, so
+ * make that first call before any stream capture.  A first call that fails
+ * leaves the device not set up, and the next call repeats the set-up.  Every call shares the array and zeroes its
  * work counters on `stream`: calls whose work overlaps on the GPU race, so the
  * caller must order them (for example by issuing them on one stream). */
 #define QEC_STATIC_SCRATCH_BYTES (80LL * 1024 * 1024)

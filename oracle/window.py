@@ -28,6 +28,31 @@ import numpy as np
 from .oracle import OracleGraph
 
 
+def window_graph(g, first_layer: int, num_layers: int):
+    """The oracle's window graph: detector layers [first_layer, first_layer +
+    num_layers) of a stream graph g (physical edge lists u, v, w, obs and nz
+    detectors per layer, as built by the input generator).  Every physical edge
+    whose detector endpoints all lie in those layers is kept (a boundary edge
+    counts when its one detector does), in the stream's order, with detectors
+    renumbered from 0; edges that leave the window are dropped.  Returns
+    (num_detectors, u, v, w, obs, edge_map) with edge_map the stream index of
+    every kept edge."""
+    nz = g.nz
+    lo = first_layer * nz
+    hi = min(g.num_detectors, (first_layer + num_layers) * nz)
+    keep = []
+    for e in range(g.u.shape[0]):
+        a, b = int(g.u[e]), int(g.v[e])
+        if lo <= a < hi and (b < 0 or lo <= b < hi):
+            keep.append(e)
+    keep = np.asarray(keep, np.int64)
+    u = g.u[keep].astype(np.int64) - lo
+    v = g.v[keep].astype(np.int64)
+    v = np.where(v >= 0, v - lo, -1)
+    return (hi - lo, u.astype(np.int32), v.astype(np.int32), g.w[keep].astype(np.int32),
+            g.obs[keep].astype(np.uint64), keep)
+
+
 def windows(num_layers: int, W: int, C: int):
     """(first layer, layers, is last) of each window over num_layers layers."""
     if not (1 <= C <= W):
@@ -47,15 +72,13 @@ def sliding_window_decode(stream, syn: np.ndarray, W: int, C: int, mode: str = "
     by window.  Returns (obs uint64 [S], status int32 [S]) and, with
     return_edges, per shot the committed edges as (u, v) stream detector pairs
     (v = -1 for a boundary edge)."""
-    from synth import unpack_defects, window_graph
-
     nz = stream.nz
     layers = stream.num_detectors // nz
     plan = windows(layers, W, C)
     graphs = []
     for a, nl, last in plan:
-        wg, _ = window_graph(stream, a, nl)
-        og = OracleGraph.from_phys(wg)
+        n, u, v, w, o, _ = window_graph(stream, a, nl)
+        og = OracleGraph(n, u, v, w, o)
         mu, mv, _, mo = og.merged_edges()
         graphs.append((a, nl, last, og, mu, mv, mo))
     S = syn.shape[0]
@@ -63,8 +86,8 @@ def sliding_window_decode(stream, syn: np.ndarray, W: int, C: int, mode: str = "
     status = np.zeros(S, np.int32)
     edges = []
     for s in range(S):
-        defects = np.zeros(stream.num_detectors, np.uint8)
-        defects[unpack_defects(syn[s], stream.num_detectors)] = 1
+        bits = np.unpackbits(np.ascontiguousarray(syn[s], np.uint32).view(np.uint8), bitorder="little")
+        defects = bits[:stream.num_detectors].astype(np.uint8)
         carry = np.zeros(stream.num_detectors, np.uint8)
         o = 0
         committed = []

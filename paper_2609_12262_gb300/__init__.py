@@ -42,7 +42,8 @@ class qec_graph_info(C.Structure):
         ("num_detectors", C.c_int32), ("num_merged_edges", C.c_int32), ("words_per_shot", C.c_int32),
         ("wmax_internal", C.c_int32), ("num_levels", C.c_int32),
         ("d_k", C.c_int64 * 8), ("b_k", C.c_int64 * 8), ("device", C.c_int32),
-        ("has_internal_obs", C.c_int32),
+        ("has_internal_obs", C.c_int32), ("components", C.c_int32), ("upper_single_cluster", C.c_int32),
+        ("distance_bound", C.c_int64),
     ]
 
 
@@ -73,6 +74,7 @@ def lib():
     L.qec_version.restype = C.c_char_p
     L.qec_schedule.argtypes = [C.c_int32, P(qec_params), P(C.c_int64), P(C.c_int64), C.c_int32]
     L.qec_graph_create.argtypes = [P(qec_graph_desc), P(vp)]
+    L.qec_graph_create_window.argtypes = [vp, C.c_int32, C.c_int32, P(qec_params), P(vp)]
     L.qec_graph_destroy.argtypes = [vp]
     L.qec_graph_get_info.argtypes = [vp, P(qec_graph_info)]
     L.qec_graph_merged_edges.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_uint64)]
@@ -163,6 +165,28 @@ class Graph:
     @classmethod
     def from_phys(cls, g, **kw):
         return cls(g.num_detectors, g.u, g.v, g.w, g.obs, **kw)
+
+    @classmethod
+    def window(cls, stream, first_detector: int, num_detectors: int):
+        """qec_graph_create_window: the induced subgraph of the Graph `stream` on
+        detectors [first_detector, first_detector + num_detectors), renumbered
+        from 0, with the stream graph's schedule parameters."""
+        h = C.c_void_p()
+        _check(lib().qec_graph_create_window(stream.handle, int(first_detector), int(num_detectors), None,
+                                             C.byref(h)))
+        return cls._wrap(h)
+
+    @classmethod
+    def _wrap(cls, h):
+        self = cls.__new__(cls)
+        self._h = h
+        self._params = None
+        info = qec_graph_info()
+        _check(lib().qec_graph_get_info(h, C.byref(info)))
+        self.info = info
+        self.num_detectors = info.num_detectors
+        self.words = info.words_per_shot
+        return self
 
     def set_commit_region(self, bitmap=None):
         """qec_graph_set_commit_region: uint32 detector bitmap (words_per_shot words) or None."""

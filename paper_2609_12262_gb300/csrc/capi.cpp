@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -37,6 +38,11 @@ struct qec_graph {
     unsigned long long *d_eobs = nullptr;
     int2 *d_eend = nullptr;
     unsigned *d_commit = nullptr;   // commit-region bitmap (sliding windows)
+    int components = 0;             // connected components of the detector graph
+    long long diam_ub = 0;          // upper bound on detector-detector distances (internal units)
+    int upper_single = 0;           // every event above level 1 forms one processing cluster
+    qec_params params{};            // Algorithm 3 inputs given at creation
+    bool has_params = false;
     DGraph dg{};
 };
 
@@ -194,6 +200,71 @@ struct PhysKey {
     int lo, hi, w, idx;
 };
 
+// Exact single-source distances over detector-detector slots (boundary
+// vertices are leaves, so no path passes through them).
+void dijkstra_host(const std::vector<int> &row, const std::vector<Slot> &slots, int src, std::vector<long long> &dist) {
+    const long long INF = LLONG_MAX;
+    std::fill(dist.begin(), dist.end(), INF);
+    using Item = std::pair<long long, int>;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+    dist[(size_t)src] = 0;
+    pq.push({0, src});
+    while (!pq.empty()) {
+        const Item it = pq.top();
+        pq.pop();
+        if (it.first != dist[(size_t)it.second]) continue;
+        for (int j = row[(size_t)it.second]; j < row[(size_t)it.second + 1]; j++) {
+            const Slot sl = slots[(size_t)j];
+            if (sl.code < 0) continue;
+            const long long nd = it.first + sl.w;
+            if (nd < dist[(size_t)sl.code]) {
+                dist[(size_t)sl.code] = nd;
+                pq.push({nd, sl.code});
+            }
+        }
+    }
+}
+
+// Connected components of the detector graph and an upper bound on the
+// distance between two detectors of one component: 2 x the eccentricity of a
+// central vertex (triangle inequality through it).  Three Dijkstra runs per
+// component: from its first vertex v, from the vertex x farthest from v, and
+// from the vertex c minimising max(d(v, c), d(x, c)).
+void graph_extent(int n, const std::vector<int> &row, const std::vector<Slot> &slots, int &components,
+                  long long &diam_ub) {
+    std::vector<int> comp((size_t)n, -1);
+    std::vector<long long> dv((size_t)n), dx((size_t)n), dc((size_t)n);
+    components = 0;
+    diam_ub = 0;
+    for (int v = 0; v < n; v++) {
+        if (comp[(size_t)v] >= 0) continue;
+        dijkstra_host(row, slots, v, dv);
+        int x = v;
+        for (int y = 0; y < n; y++)
+            if (dv[(size_t)y] != LLONG_MAX) {
+                comp[(size_t)y] = components;
+                if (dv[(size_t)y] > dv[(size_t)x]) x = y;
+            }
+        dijkstra_host(row, slots, x, dx);
+        int c = v;
+        long long best = LLONG_MAX;
+        for (int y = 0; y < n; y++)
+            if (comp[(size_t)y] == components) {
+                const long long m = std::max(dv[(size_t)y], dx[(size_t)y]);
+                if (m < best) { best = m; c = y; }
+            }
+        dijkstra_host(row, slots, c, dc);
+        long long ecc_v = 0, ecc_c = 0;
+        for (int y = 0; y < n; y++)
+            if (comp[(size_t)y] == components) {
+                ecc_v = std::max(ecc_v, dv[(size_t)y]);
+                ecc_c = std::max(ecc_c, dc[(size_t)y]);
+            }
+        diam_ub = std::max(diam_ub, 2 * std::min(ecc_v, ecc_c));
+        components++;
+    }
+}
+
 // ------------------------------------------------------------ workspace --
 struct Workspace {
     int device = -1;
@@ -321,6 +392,11 @@ int qec::graph_device_view(const qec_graph *g, DGraph *out, int *device) {
     return QEC_OK;
 }
 
+qec_tuning qec::current_tuning() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune;
+}
+
 int qec::set_last_error(int code, const char *msg) {
     g_err = msg ? msg : "";
     return code;
@@ -403,6 +479,7 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
         g->ew.push_back(2 * keys[i].w);
         g->eobs.push_back(desc->obs[keys[i].idx]);
     }
+    if (desc->params) { g->params = *desc->params; g->has_params = true; }
     g->n = n;
     g->m = (int)g->eu.size();
     g->words = ((n + 31) / 32 + 3) / 4 * 4;
@@ -471,6 +548,20 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
         for (int e = 0; e < g->m; e++) wmin = std::min<long long>(wmin, g->ew[e]);
         d.hop2 = (g->m > 0 && 3 * wmin > (long long)d.b1) ? 1 : 0;
     }
+    // Algorithm 1 above level 1: with one connected component and b_2 at least
+    // the distance bound, every residual event links to every other at level
+    // 2, so all of them form one component; it is accepted at the first level
+    // k >= 2 whose d_k covers the bound (twice the bound plus the largest
+    // weight also covers every boundary contact).  Then the events left after
+    // level 1 form exactly one processing cluster.
+    graph_extent(n, row, slots, g->components, g->diam_ub);
+    {
+        bool links = g->num_levels >= 2 && g->bk[1] >= g->diam_ub;
+        bool accepted = false;
+        for (int k = 1; k < g->num_levels; k++)
+            if (g->dk[k] >= 2 * (g->diam_ub + g->wmax)) accepted = true;
+        g->upper_single = (g->components == 1 && links && accepted) ? 1 : 0;
+    }
     d.row = g->d_row;
     d.slot = g->d_slot;
     d.eobs = g->d_eobs;
@@ -478,6 +569,40 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
     d.seid = g->d_seid;
     *out = g;
     return QEC_OK;
+}
+
+int qec_graph_create_window(const qec_graph *stream, int32_t first_detector, int32_t num_detectors,
+                            const qec_params *params, qec_graph **out) {
+    if (!out) return fail(QEC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!stream) return fail(QEC_EINVAL, "stream graph is NULL");
+    if (first_detector < 0 || num_detectors < 1 || (long long)first_detector + num_detectors > stream->n)
+        return fail(QEC_ERANGE, "window detector range outside the stream graph");
+    const int lo = first_detector, hi = first_detector + num_detectors;
+    // induced subgraph: merged edges with every detector endpoint inside the
+    // window, renumbered from 0 in the same order (the stream graph has no
+    // parallel edges left, so merging the window again changes nothing)
+    std::vector<int> u, v, w;
+    std::vector<uint64_t> o;
+    for (int e = 0; e < stream->m; e++) {
+        const int a = stream->eu[e], b = stream->ev[e];
+        if (a < lo || a >= hi || (b >= 0 && (b < lo || b >= hi))) continue;
+        u.push_back(a - lo);
+        v.push_back(b >= 0 ? b - lo : -1);
+        w.push_back(stream->ew[e] / 2);   // internal weights are twice the integer weights
+        o.push_back(stream->eobs[e]);
+    }
+    qec_graph_desc d;
+    std::memset(&d, 0, sizeof(d));
+    d.num_detectors = num_detectors;
+    d.num_edges = (int)u.size();
+    d.num_observables = QEC_MAX_OBSERVABLES;   // masks were validated when the stream graph was created
+    d.u = u.data();
+    d.v = v.data();
+    d.w = w.data();
+    d.obs = o.data();
+    d.params = params ? params : (stream->has_params ? &stream->params : nullptr);
+    return qec_graph_create(&d, out);
 }
 
 int qec_graph_destroy(qec_graph *g) {
@@ -530,6 +655,9 @@ int qec_graph_get_info(const qec_graph *g, qec_graph_info *out) {
     for (int i = 0; i < g->num_levels && i < 8; i++) { out->d_k[i] = g->dk[i]; out->b_k[i] = g->bk[i]; }
     out->device = g->device;
     out->has_internal_obs = g->internal_obs;
+    out->components = g->components;
+    out->distance_bound = g->diam_ub;
+    out->upper_single_cluster = g->upper_single;
     return QEC_OK;
 }
 

@@ -77,36 +77,43 @@ int qec_decode_batch_static(const qec_graph *const *graphs, int32_t num_graphs, 
     const long long slab = qec::slab_bytes_for(caps);
     if (kQueueBytes + kOverflowBytes + slab * kWarps > kScratchBytes)
         return err(QEC_ERANGE, "static scratch too small for its slabs");
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char *base = nullptr;
-    bool fill = false;
     {
-        // set-up, once per device, with that device current
+        // set-up, once per device, with that device current: look up the
+        // array's device address, then fill the slabs with all-ones (empty
+        // table entries, which the kernel expects and leaves behind).  The
+        // device counts as set up only once that fill is enqueued, so a failed
+        // first call is repeated in full by the next one.
         std::lock_guard<std::mutex> lk(g_mu);
         DevState &s = g_state[dev];
         if (!s.ready) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            ce = cudaStreamIsCapturing(st, &cs);
+            if (ce != cudaSuccess)
+                return err(QEC_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+            if (cs != cudaStreamCaptureStatusNone)
+                return err(QEC_EINVAL, "the first qec_decode_batch_static call on a device must not be captured");
             void *p = nullptr;
             ce = cudaGetSymbolAddress(&p, g_static_scratch);
             if (ce != cudaSuccess || !p)
                 return err(QEC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
+            ce = cudaMemsetAsync(static_cast<char *>(p) + kQueueBytes + kOverflowBytes, 0xff,
+                                 (size_t)(slab * kWarps), st);
+            if (ce != cudaSuccess) return err(QEC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(ce));
             s.base = static_cast<char *>(p);
             s.ready = true;
-            fill = true;
         }
         base = s.base;
-    }
-    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (fill) {
-        // the kernel expects empty (all-ones) table entries and leaves them so
-        ce = cudaMemsetAsync(base + kQueueBytes + kOverflowBytes, 0xff, (size_t)(slab * kWarps), st);
-        if (ce != cudaSuccess) return err(QEC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(ce));
     }
     auto *queue = reinterpret_cast<unsigned long long *>(base);
     ce = cudaMemsetAsync(queue, 0, 4 * sizeof(unsigned long long), st);   // counters start at zero
     if (ce != cudaSuccess) return err(QEC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(ce));
+    const qec_tuning tune = qec::current_tuning();
     a.num_graphs = num_graphs;
-    a.band_factor = 1;
+    a.band_factor = tune.band_factor > 0 ? tune.band_factor : 1;
     a.num_shots = num_shots;
-    a.max_events = 4000000;
+    a.max_events = tune.max_events > 0 ? tune.max_events : 4000000;
     a.graph_of_shot = graph_of_shot;
     a.syn_off = reinterpret_cast<const long long *>(syn_offset_words);
     a.syn = syndromes;
@@ -121,7 +128,8 @@ int qec_decode_batch_static(const qec_graph *const *graphs, int32_t num_graphs, 
     a.pass = 0;
     a.single_shot = -1;
     a.watchdog_ns = 60LL * 1000 * 1000 * 1000;
-    ce = qec::launch_batch(a, kWarps / 4, 128, st);
+    // one warp per block, so that the persistent warps spread over every SM
+    ce = qec::launch_batch(a, kWarps, 32, st);
     if (ce != cudaSuccess) return err(QEC_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(ce));
     return QEC_OK;
 }

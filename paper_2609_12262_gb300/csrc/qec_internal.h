@@ -102,6 +102,9 @@ int occupancy_blocks(int block_threads);
 int max_block_threads();
 // Device view and device id of a created graph (QEC_EINVAL for NULL).
 int graph_device_view(const qec_graph *g, DGraph *out, int *device);
+// The tuning knobs currently set by qec_set_tuning (band width and event
+// budget apply to every batched entry point).
+qec_tuning current_tuning();
 // Record the calling thread's error text for qec_last_error; returns code.
 int set_last_error(int code, const char *msg);
 

@@ -21,7 +21,7 @@ def shard(num_units: int, world_size: int, rank: int) -> tuple[int, int]:
 
 
 def shard_seed(seed: int, rank: int) -> int:
-    """Seed of rank `rank`'s independent synthetic batch (weak scaling)."""
+    """Seed of rank `rank`'s own generated input batch (weak scaling)."""
     return seed + 1000 * rank
 
 

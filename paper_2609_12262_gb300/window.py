@@ -1,13 +1,13 @@
 """Sliding-window decoding of long syndrome histories through the C ABI.
 
 Windows of W detector layers start every C layers; window k's graph is the
-induced subgraph of the stream graph on its layers, with the first C layers as
-its commit region (every layer for the last window).  For each window the
-library assembles the window syndromes on the device (stream bits of its layers
-XOR the previous window's carry) and decodes them, XOR-accumulating the
-committed observable; the committed edges leaving the region flip detectors of
-the next window (qec_decode_window_batch, qec_window_assemble).  This module
-only sequences those calls.
+induced subgraph of the stream graph on its layers (qec_graph_create_window),
+with the first C layers as its commit region (every layer for the last window).
+For each window the library assembles the window syndromes on the device
+(stream bits of its layers XOR the previous window's carry) and decodes them,
+XOR-accumulating the committed observable; the committed edges leaving the
+region flip detectors of the next window (qec_decode_window_batch,
+qec_window_assemble).  This module only sequences those calls.
 """
 
 from __future__ import annotations
@@ -30,20 +30,22 @@ def plan(num_layers: int, W: int, C: int):
 
 
 class SlidingWindow:
-    """Decoder for many streams of one stream graph (a synth PhysGraph of the
-    whole history, detectors numbered layer by layer, nz per layer)."""
+    """Decoder for many streams of one stream graph: `stream` is a Graph of the
+    whole history whose detectors are numbered layer by layer, `layer_size`
+    detectors per layer."""
 
-    def __init__(self, stream, W: int, C: int):
-        from synth import window_graph
+    def __init__(self, stream: Graph, layer_size: int, W: int, C: int):
+        n = stream.num_detectors
+        if layer_size < 1 or n % layer_size:
+            raise ValueError("the stream's detectors must form whole layers of layer_size")
         self.stream = stream
-        self.nz = stream.nz
+        self.nz = int(layer_size)
         self.W, self.C = W, C
         self.windows = []
-        for a, nl, last in plan(stream.num_detectors // self.nz, W, C):
-            wg, _ = window_graph(stream, a, nl)
-            g = Graph.from_phys(wg)
+        for a, nl, last in plan(n // self.nz, W, C):
+            g = Graph.window(stream, a * self.nz, nl * self.nz)
             bits = np.zeros(g.words * 32, np.uint8)
-            bits[:(wg.num_detectors if last else C * self.nz)] = 1
+            bits[:(g.num_detectors if last else C * self.nz)] = 1
             g.set_commit_region(np.packbits(bits, bitorder="little").view(np.uint32))
             self.windows.append((a, nl, last, g))
 

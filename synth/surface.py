@@ -207,31 +207,6 @@ def pack_defects(defects, n: int) -> np.ndarray:
     return np.packbits(bits, bitorder="little").view(np.uint32).copy()
 
 
-def window_graph(g: PhysGraph, first_layer: int, num_layers: int):
-    """The window of detector layers [first_layer, first_layer + num_layers) of a
-    stream graph g: the induced subgraph (edges with every detector endpoint
-    inside the window; boundary edges of window detectors), detectors renumbered
-    from 0 in the same order.  Edges that leave the window (the time edges to the
-    layers just below and above it) are not part of it.
-
-    Returns (window PhysGraph, edge_map int64 [window edges] = index of each
-    window edge in g)."""
-    nz = g.nz
-    lo = first_layer * nz
-    hi = min(g.num_detectors, (first_layer + num_layers) * nz)
-    inside_u = (g.u >= lo) & (g.u < hi)
-    inside_v = (g.v < 0) | ((g.v >= lo) & (g.v < hi))
-    keep = np.nonzero(inside_u & inside_v)[0]
-    n = hi - lo
-    words = ((n + 31) // 32 + 3) // 4 * 4
-    v = g.v[keep].copy()
-    v[v >= 0] -= lo
-    wg = PhysGraph(d=g.d, rounds=(hi - lo) // nz - 1, num_detectors=n, nz=nz,
-                   u=(g.u[keep] - lo).astype(np.int32), v=v.astype(np.int32), w=g.w[keep].copy(),
-                   obs=g.obs[keep].copy(), p=g.p[keep].copy(), kind=g.kind[keep].copy(), words=words)
-    return wg, keep.astype(np.int64)
-
-
 def mixed_batch(ds, shots_per_d: int, p: float, seed: int):
     """Mixed-distance batch (d rounds each), shot order shuffled by a seeded permutation.
 

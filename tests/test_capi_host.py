@@ -123,3 +123,29 @@ def test_window_assemble_validates_before_touching_memory(L):
     rc = L.qec_window_assemble(None, 8, 0, 10, None, 0, 0, 0, fake, 8, 4, None)
     assert rc == q.QEC_EINVAL
     assert L.qec_window_assemble(fake, 8, 0, 10, None, 0, 0, 0, fake, 8, 0, None) == q.QEC_OK   # no rows
+
+
+def test_static_entry_point_failure_leaves_no_half_set_up_state(L):
+    """Without a usable CUDA device the static-scratch entry point fails before
+    its one-time set-up (the device is marked set up only after the fill of its
+    array has been enqueued), so every later call fails the same way instead of
+    decoding against an unfilled array.  Argument errors come first."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    vp = C.c_void_p
+    fake = vp(16)
+    arr = (vp * 1)(fake)
+    assert L.qec_decode_batch_static(arr, 1, None, None, fake, -1, fake, fake, fake, None) == q.QEC_EINVAL
+    assert L.qec_decode_batch_static(arr, 1, None, None, fake, (1 << 20) + 1, fake, fake, fake, None) == q.QEC_ERANGE
+    assert L.qec_decode_batch_static(arr, 1, None, None, None, 4, fake, fake, fake, None) == q.QEC_EINVAL
+    for _ in range(2):
+        rc = L.qec_decode_batch_static(arr, 1, None, None, fake, 4, fake, fake, fake, None)
+        assert rc == q.QEC_ECUDA
+        assert "cudaGetDevice" in q.last_error()
+
+
+def test_window_graph_validates_on_the_host(L):
+    h = C.c_void_p()
+    assert L.qec_graph_create_window(None, 0, 4, None, C.byref(h)) == q.QEC_EINVAL and not h.value
+    assert L.qec_graph_create_window(C.c_void_p(16), 0, 4, None, None) == q.QEC_EINVAL

@@ -56,9 +56,16 @@ def test_circuit_level_diagnostics(qd):
         o, w, s, dg = qd.decode_batch_ex([qg], t, mode=mode)
         torch.cuda.synchronize()
         D = dg.cpu().numpy()
+        W, O, S = w.cpu().numpy(), qd.to_uint64(o), s.cpu().numpy()
+        multi = 0
         for i in range(300):
             r = og.diag(unpack_defects(syn[i], g.num_detectors), mode)
+            assert (int(W[i]), int(O[i]), int(S[i])) == (r["weight"], r["obs"], r["status"]), (mode, i)
             if r["clusters_above_l1"] > 1:
+                multi += 1
                 continue
-            got = (int(w[i]), int(D[i, 0]), int(D[i, 1]), int(D[i, 2]))
-            assert got == (r["weight"], r["e_ideal"], r["t_ideal"], r["events"]), (mode, i)
+            got = (int(D[i, 0]), int(D[i, 1]), int(D[i, 2]), int(D[i, 3]), int(D[i, 4]), int(D[i, 7]))
+            exp = (r["e_ideal"], r["t_ideal"], r["events"], r["l1_clusters"], r["l1_defects"], r["defects"])
+            assert got == exp, (mode, i, got, exp)
+        assert multi == 0
+    assert qg.info.upper_single_cluster == 1

@@ -224,3 +224,42 @@ def test_large_windows_match_oracle(qd, d, p, shots):
     gpu = gpu_decode(qd, g, syn)
     ref = oracle_decode([pg], np.zeros(shots, np.int32), list(syn), chunk=1)
     assert_same(gpu, ref, "d%d p%g" % (d, p))
+
+
+@pytest.mark.parametrize("d,p,shots", [(41, 0.003, 4), (41, 0.005, 4), (51, 0.003, 3), (51, 0.005, 3)])
+def test_large_windows_at_higher_rates(qd, d, p, shots):
+    """The scaling study's largest windows at p = 0.003 and 0.005, where the
+    top-level cluster is largest (500 - 2,000 detection events per window)."""
+    pg = rotated_surface_code(d, d, p)
+    g = qd.Graph.from_phys(pg)
+    syn, _ = sample_shots(pg, shots, 2000 + d + int(p * 1e4))
+    gpu = gpu_decode(qd, g, syn)
+    ref = oracle_decode([pg], np.zeros(shots, np.int32), list(syn), chunk=1)
+    assert np.all(ref[2] == 0)
+    assert_same(gpu, ref, "d%d p%g" % (d, p))
+
+
+def test_overflow_pass_decodes_shots_beyond_the_main_slab(qd):
+    """With a small main-pass slab (kcap events), shots with more detection
+    events than kcap fail in the main pass and are decoded by the overflow pass
+    (room for 4 kcap events); shots beyond that end with QEC_SHOT_CAPACITY."""
+    pg = rotated_surface_code(15, 15, 0.008)
+    g = qd.Graph.from_phys(pg)
+    syn, _ = sample_shots(pg, 400, 61)
+    K = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)
+    ref = oracle_decode([pg], np.zeros(400, np.int32), list(syn))
+    try:
+        qd.set_tuning(kcap=40)
+        gpu = gpu_decode(qd, g, syn)
+        # overflow slabs hold 4 x 40 = 160 events: every shot here fits there
+        assert K.max() <= 160 and np.count_nonzero(K > 40) >= 50
+        assert_same(gpu, ref, "overflow pass")
+        qd.set_tuning(kcap=16)
+        small = gpu_decode(qd, g, syn)
+    finally:
+        qd.set_tuning(kcap=-1)
+    over = K > 64
+    assert np.count_nonzero(over) >= 50
+    assert np.all(small[2][over] == qd.SHOT_CAPACITY)
+    ok = ~over
+    assert_same(tuple(x[ok] for x in small), tuple(x[ok] for x in ref), "overflow pass, small slabs")

@@ -6,7 +6,8 @@ GB300."""
 import numpy as np
 import pytest
 
-from oracle.window import sliding_window_decode
+from oracle import OracleGraph
+from oracle.window import sliding_window_decode, window_graph
 from synth import rotated_surface_code, rotated_surface_code_circuit, sample_shots
 
 pytestmark = pytest.mark.gpu
@@ -80,7 +81,7 @@ def test_sliding_window_matches_oracle(qd, name, kw, W, C, S):
         S = len(pick)
     else:
         syn, _ = sample_shots(g, S, 23)
-    dec = SlidingWindow(g, W, C)
+    dec = SlidingWindow(qd.Graph.from_phys(g), g.nz, W, C)
     t = torch.from_numpy(syn.view(np.int32).reshape(-1)).cuda()
     obs, st = dec.decode(t, S)
     torch.cuda.synchronize()
@@ -110,3 +111,32 @@ def test_window_decode_needs_a_commit_region(qd):
     g.set_commit_region(None)
     with pytest.raises(qd.QecError):
         qd.decode_window_batch([g], rows, obs, carry, st, num_shots=S)
+
+
+@pytest.mark.parametrize("circuit", [False, True])
+def test_window_graph_matches_the_oracle_window(qd, circuit):
+    """qec_graph_create_window (the library's induced subgraph of a stream graph)
+    against the oracle's own window construction, merged edge by merged edge
+    (endpoints, internal weight, observable) and schedule."""
+    g = rotated_surface_code_circuit(5, 12, 0.003) if circuit else rotated_surface_code(7, 20, 0.004)
+    stream = qd.Graph.from_phys(g)
+    for a, nl in ((0, 6), (3, 5), (7, 6), (0, g.num_detectors // g.nz)):
+        if a + nl > g.num_detectors // g.nz:
+            continue
+        win = qd.Graph.window(stream, a * g.nz, nl * g.nz)
+        n, u, v, w, o, _ = window_graph(g, a, nl)
+        og = OracleGraph(n, u, v, w, o)
+        assert win.num_detectors == n
+        got = win.merged_edges()
+        exp = og.merged_edges()
+        assert all(np.array_equal(np.asarray(x, np.int64), np.asarray(y, np.int64)) for x, y in zip(got[:3], exp[:3]))
+        assert np.array_equal(got[3], exp[3])
+        assert list(win.schedule()[0]) == [int(x) for x in og.dk[:len(win.schedule()[0])]]
+
+
+def test_window_graph_rejects_bad_ranges(qd):
+    stream = qd.Graph.from_phys(rotated_surface_code(5, 5, 0.01))
+    n = stream.num_detectors
+    for first, num in ((-1, 4), (0, 0), (n - 3, 4), (0, n + 1)):
+        with pytest.raises(qd.QecError):
+            qd.Graph.window(stream, first, num)

@@ -9,8 +9,8 @@ import numpy as np
 import pytest
 
 from oracle import OracleGraph
-from oracle.window import sliding_window_decode, windows
-from synth import rotated_surface_code, rotated_surface_code_circuit, sample_shots, unpack_defects, window_graph
+from oracle.window import sliding_window_decode, window_graph, windows
+from synth import rotated_surface_code, rotated_surface_code_circuit, sample_shots, unpack_defects
 
 
 def test_window_plan_tiles_the_layers():
@@ -26,13 +26,20 @@ def test_window_plan_tiles_the_layers():
 
 def test_window_graph_is_the_induced_subgraph():
     g = rotated_surface_code(5, 12, 0.01)
-    wg, emap = window_graph(g, 4, 5)
+    n, u, v, w, o, emap = window_graph(g, 4, 5)
     lo, hi = 4 * g.nz, 9 * g.nz
-    assert wg.num_detectors == hi - lo
-    inside = [(u, v) for u, v in zip(g.u, g.v) if lo <= u < hi and (v < 0 or lo <= v < hi)]
-    assert len(inside) == wg.num_edges
-    assert np.array_equal(g.u[emap] - lo, wg.u)
-    assert np.array_equal(g.w[emap], wg.w) and np.array_equal(g.obs[emap], wg.obs)
+    assert n == hi - lo
+    inside = [(a, b) for a, b in zip(g.u, g.v) if lo <= a < hi and (b < 0 or lo <= b < hi)]
+    assert len(inside) == u.shape[0]
+    assert np.array_equal(g.u[emap] - lo, u)
+    assert np.array_equal(np.where(g.v[emap] >= 0, g.v[emap] - lo, -1), v)
+    assert np.array_equal(g.w[emap], w) and np.array_equal(g.obs[emap], o)
+    # a window of the rotated code over layers [a, a + L) is the code's own graph
+    # with L - 1 noisy rounds, apart from the perfect last round: same counts of
+    # space edges per layer (d*d) and time edges between its layers (nz each)
+    assert u.shape[0] == 5 * 25 + 4 * g.nz
+    # the first and last layers are cut off from the layers beyond them
+    assert not np.any((g.u[emap] < lo) | (g.u[emap] >= hi))
 
 
 @pytest.mark.parametrize("d,R,p,shots", [(5, 10, 0.01, 80), (7, 7, 0.005, 60)])

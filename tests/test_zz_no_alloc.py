@@ -9,6 +9,9 @@ first failure has already run every other test.
 """
 
 import ctypes as C
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -90,3 +93,51 @@ def test_static_capacity_and_limits(qd):
                                    C.c_void_p(small.data_ptr()), None)
     assert rc == qd.QEC_ERANGE
     assert "QEC_STATIC_MAX_SHOTS" in qd.last_error()
+
+
+_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_2609_12262_gb300 as q
+from synth import mixed_batch
+from tests.oracle_pool import oracle_decode
+graphs, gid, offs, syn = mixed_batch([5, 9, 13], 300, 0.004, seed=91)
+gg = [q.Graph.from_phys(g) for g in graphs]
+S = gid.shape[0]
+t_syn = torch.from_numpy(syn.view(np.int32)).cuda()
+t_gid = torch.from_numpy(gid.astype(np.int32)).cuda()
+t_off = torch.from_numpy(offs.astype(np.int64)).cuda()
+out = (torch.empty(S, dtype=torch.int64, device="cuda"), torch.empty(S, dtype=torch.int64, device="cuda"),
+       torch.empty(S, dtype=torch.int32, device="cuda"))
+side = torch.cuda.Stream()
+# the first decode of this process goes through the static entry point
+q.decode_batch_static(gg, t_syn, t_gid, t_off, num_shots=S, out=out, stream=side)
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+res = []
+for i in range(3):
+    q.decode_batch_static(gg, t_syn, t_gid, t_off, num_shots=S, out=out, stream=side if i % 2 else None)
+    torch.cuda.synchronize()
+    res.append((out[1].cpu().numpy().copy(), q.to_uint64(out[0]).copy(), out[2].cpu().numpy().copy()))
+free1 = torch.cuda.mem_get_info()[0]
+rows = [syn[offs[s]:offs[s] + graphs[gid[s]].words] for s in range(S)]
+ref = oracle_decode(graphs, gid, rows, workers=1)
+same = all(all(np.array_equal(a, b) for a, b in zip(r, ref)) for r in res)
+print("RESULT", free0 - free1, int(same), int(np.count_nonzero(ref[2])))
+"""
+
+
+def test_static_allocates_nothing_and_matches_oracle_in_a_fresh_process():
+    """In a fresh process whose first decode is the static entry point: free
+    device memory is unchanged over three more calls (one on a non-default
+    stream), and every call equals the oracle shot by shot."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _CHILD, root], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [x for x in r.stdout.splitlines() if x.startswith("RESULT")][-1].split()
+    grew, same, bad = int(line[1]), int(line[2]), int(line[3])
+    assert grew == 0, "device memory changed by %d bytes" % grew
+    assert same == 1 and bad == 0
