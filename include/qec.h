@@ -104,10 +104,10 @@ typedef struct {
     int32_t has_internal_obs;  /* some detector-detector edge carries an observable */
     int32_t components;        /* connected components of the detector graph */
     int32_t upper_single_cluster; /* 1: every detection event left after level 1
-                                  * forms one processing cluster (one component,
-                                  * b_2 >= distance_bound, and a later d_k covers
-                                  * it); the hierarchical execution is then level 1
-                                  * plus one top-level cluster exactly */
+                                  * forms one processing cluster (one component
+                                  * and b_2 >= distance_bound); the hierarchical
+                                  * execution is then level 1 plus one top-level
+                                  * cluster exactly */
     int64_t distance_bound;    /* upper bound on the distance between two connected
                                 * detectors, internal units */
 } qec_graph_info;
@@ -293,14 +293,24 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
  * binding; all have safe defaults).  In qec_set_tuning a positive value sets
  * a knob, zero keeps its current value and a negative value restores the
  * default (warps_per_block 4, blocks_per_sm 0 = as many as fit, band_factor 1,
- * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, max_events 4e6).
- * qec_get_tuning reports 0 for the automatic choices. */
+ * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, max_events 4e6,
+ * team_warps 0 = automatic, team_min_detectors 2048).
+ * qec_get_tuning reports 0 for the automatic choices.
+ *
+ * team_warps is the number of warps that decode one shot together: 1 = one warp
+ * per shot (the throughput path: as many shots in flight as warps fit), 4 or
+ * 16 = one thread block of that many warps per shot (every step of the shot
+ * spread over the block: the latency path for large windows).  Automatic: 16
+ * when a batch has fewer shots than the GPU has SMs and its largest graph has
+ * at least team_min_detectors detectors, else 1.  Results do not depend on it. */
 typedef struct {
     int32_t warps_per_block;   /* 1 .. 32 */
     int32_t blocks_per_sm;     /* 1 .. 64 */
     int32_t band_factor;       /* flooder band width in units of the largest weight, 1 .. 64 */
     int32_t kcap;              /* detection events per shot held by a main-pass slab */
     int64_t max_events;        /* event budget per shot */
+    int32_t team_warps;        /* 1, 4 or 16; 0 = automatic */
+    int32_t team_min_detectors;   /* automatic team choice: smallest graph for a block per shot */
 } qec_tuning;
 int qec_set_tuning(const qec_tuning *t);
 int qec_get_tuning(qec_tuning *t);

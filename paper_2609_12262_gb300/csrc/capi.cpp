@@ -288,7 +288,7 @@ struct Workspace {
 
 Workspace g_ws[64];
 std::mutex g_tune_mu;
-qec_tuning g_tune = {4, 0, 1, 0, 4000000};
+qec_tuning g_tune = {4, 0, 1, 0, 4000000, 0, 2048};
 
 void ws_free(Workspace &w) {
     if (w.slabs) cudaFree(w.slabs);
@@ -550,17 +550,16 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
     }
     // Algorithm 1 above level 1: with one connected component and b_2 at least
     // the distance bound, every residual event links to every other at level
-    // 2, so all of them form one component; it is accepted at the first level
-    // k >= 2 whose d_k covers the bound (twice the bound plus the largest
-    // weight also covers every boundary contact).  Then the events left after
-    // level 1 form exactly one processing cluster.
+    // 2 (and at every later level, b_k grows with k), so all of them form one
+    // component at each level until it is accepted (d_k and b_k grow without
+    // bound under Algorithm 3's recursion, so it is, unless its parity can never
+    // be met).  Then the events left after level 1 form exactly one processing
+    // cluster.  b_2 is taken as b_1 when the schedule stored only one level
+    // (b_k increases with k, so this only errs on the safe side).
     graph_extent(n, row, slots, g->components, g->diam_ub);
     {
-        bool links = g->num_levels >= 2 && g->bk[1] >= g->diam_ub;
-        bool accepted = false;
-        for (int k = 1; k < g->num_levels; k++)
-            if (g->dk[k] >= 2 * (g->diam_ub + g->wmax)) accepted = true;
-        g->upper_single = (g->components == 1 && links && accepted) ? 1 : 0;
+        const long long b2 = g->num_levels >= 2 ? g->bk[1] : g->bk[0];
+        g->upper_single = (g->components == 1 && b2 >= g->diam_ub) ? 1 : 0;
     }
     d.row = g->d_row;
     d.slot = g->d_slot;
@@ -676,7 +675,9 @@ int qec_set_tuning(const qec_tuning *t) {
     if (!t) return fail(QEC_EINVAL, "NULL tuning");
     if (t->warps_per_block > 32 || t->blocks_per_sm > 64 || t->band_factor > 64 || t->kcap > (1 << 18))
         return fail(QEC_EINVAL, "tuning value out of range");
-    static const qec_tuning defaults = {4, 0, 1, 0, 4000000};
+    if (t->team_warps > 0 && t->team_warps != 1 && t->team_warps != qec::TEAM_MID && t->team_warps != qec::TEAM_BIG)
+        return fail(QEC_EINVAL, "team_warps must be 1, 4 or 16 (0 keeps, negative = automatic)");
+    static const qec_tuning defaults = {4, 0, 1, 0, 4000000, 0, 2048};
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto pick = [](auto v, auto cur, auto def) { return v > 0 ? v : (v < 0 ? def : cur); };
     g_tune.warps_per_block = pick(t->warps_per_block, g_tune.warps_per_block, defaults.warps_per_block);
@@ -684,6 +685,8 @@ int qec_set_tuning(const qec_tuning *t) {
     g_tune.band_factor = pick(t->band_factor, g_tune.band_factor, defaults.band_factor);
     g_tune.kcap = pick(t->kcap, g_tune.kcap, defaults.kcap);
     g_tune.max_events = pick(t->max_events, g_tune.max_events, defaults.max_events);
+    g_tune.team_warps = pick(t->team_warps, g_tune.team_warps, defaults.team_warps);
+    g_tune.team_min_detectors = pick(t->team_min_detectors, g_tune.team_min_detectors, defaults.team_min_detectors);
     return QEC_OK;
 }
 
@@ -747,7 +750,20 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     const int wpb = std::max(1, std::min(tune.warps_per_block, qec::max_block_threads() / 32));
     int bps = tune.blocks_per_sm;
     if (bps <= 0) bps = qec::occupancy_blocks(32 * wpb);
+    // team size: warps that decode one shot together (the sliding-window
+    // kernel is compiled for one warp per shot only)
+    int team = tune.team_warps;
+    if (team <= 0)
+        team = (!plain && num_shots < sms && nmax >= tune.team_min_detectors) ? qec::TEAM_BIG : 1;
+    if (window) team = 1;
+    // slabs: one per warp of the main pass (one warp per shot) or one per
+    // resident block (one block per shot); the overflow pass has one per SM
     long long nwarps = plain ? 1 : (long long)sms * bps * wpb;
+    long long nteams = nwarps;
+    if (team > 1 && !plain) {
+        nteams = std::min<long long>((long long)sms * qec::team_occupancy_blocks(team), std::max<long long>(num_shots, 1));
+        nwarps = std::max(nwarps, nteams);
+    }
     long long nwarps2 = plain ? 1 : (long long)sms;
     if (plain) caps = caps2;
     Workspace &w = g_ws[dev];
@@ -793,7 +809,7 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
         a.pass = 0;
         for (int64_t shot = 0; shot < num_shots; shot++) {
             a.single_shot = shot;
-            ce = qec::launch_batch(a, 1, 32, s);
+            ce = qec::launch_batch(a, 1, 32, s, team);
             if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
         }
     } else {
@@ -815,13 +831,14 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
         a.slab_bytes = w.slab_bytes;
         a.caps = w.caps;
         a.pass = 0;
-        ce = qec::launch_batch(a, (int)(nwarps / wpb), 32 * wpb, s);
+        if (team > 1) ce = qec::launch_batch(a, (int)nteams, 32 * team, s, team);
+        else ce = qec::launch_batch(a, (int)(nwarps / wpb), 32 * wpb, s);
         if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
         a.slabs = w.slabs2;
         a.slab_bytes = w.slab_bytes2;
         a.caps = w.caps2;
         a.pass = 1;
-        ce = qec::launch_batch(a, (int)nwarps2, 32, s);
+        ce = qec::launch_batch(a, (int)nwarps2, team > 1 ? 32 * team : 32, s, team);
         if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
     }
     ce = cudaEventRecord(w.done, s);

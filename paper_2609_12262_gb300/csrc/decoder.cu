@@ -1,7 +1,11 @@
-// decoder.cu -- warp-per-shot parallel sparse-blossom decoder for sm_103a.
+// decoder.cu -- parallel sparse-blossom decoder for sm_103a.
 //
-// One warp decodes one shot end to end (a persistent grid pulls shots from a
-// device work counter):
+// A team of threads decodes one shot end to end, and a persistent grid of
+// teams pulls shots from a device work counter.  A team is either one warp
+// (the batched path: thousands of shots in flight, the 32 lanes of a warp
+// working on one shot) or one whole thread block of NW warps (large windows:
+// every step below spread over all of the block's threads, for the latency of
+// a single window).
 //   1. defect compaction: the shot's syndrome bitmap is read with 16-byte
 //      vector loads and compacted by a warp prefix sum (input D of the paper's
 //      "Decoding task"; Alg. 1 input).
@@ -9,7 +13,7 @@
 //      R_s} with exact graph distances (hash table keyed by (vertex, event)),
 //      explored once its region starts growing and kept at R_s >= Rad(s) + L
 //      (L above the largest weight).  A ball is grown band by band (band >=
-//      largest weight) by warp-parallel label-correcting relaxation from the
+//      largest weight) by team-parallel label-correcting relaxation from the
 //      previous band; each new entry is checked against the other events'
 //      balls holding the same vertex, and against events sitting on it, which
 //      records the exact distance of every pair of events whose balls touch.
@@ -31,16 +35,20 @@
 //   5. Tracing: blossoms are expanded into matched event pairs and boundary
 //      matches; the weight is the sum of the tight pair / boundary distances and
 //      the observable mask the XOR of the canonical paths' masks.  The
-//      sliding-window instantiation (batch_kernel<true>) also walks every path
-//      and commits the edges that touch the window's commit region.
+//      sliding-window instantiation (batch_kernel<true, 1>) also walks every
+//      path and commits the edges that touch the window's commit region.
 //
 // Simultaneous events are applied in the canonical order (t, kind, lo, hi) with
 // kind EXTEND < IMPLODE < COLLIDE < BOUNDARY and lo, hi the ranks of the events
 // in the sorted defect list, which makes the result independent of execution
-// order and equal to global sparse blossom (Theorem 1).
+// order, of the team size and equal to global sparse blossom (Theorem 1).
 //
 // Every loop is bounded: the event budget, hash probe lengths and list
-// capacities end a shot with a status code instead of spinning.
+// capacities end a shot with a status code instead of spinning.  In a team of
+// several warps every decision that steers control flow around a team barrier
+// is taken from a team reduction or broadcast, or from shot state that no
+// thread writes between the barrier before the read and the barrier after it,
+// so all threads of a team always take the same path.
 //
 // The rarely taken matcher steps (augment, blossom, shatter), the tracing and
 // the level-1 neighbourhood searches are kept out of line (__noinline__): the
@@ -74,9 +82,9 @@ constexpr long long T_MAX = (1LL << 26) - 1;
 
 enum { MATE_NONE = -1, MATE_BOUNDARY = -2 };
 
-// slab counters
+// slab counters (C_R0 .. C_NEXT: work-list counters of multi-warp teams)
 enum { C_ECOUNT = 0, C_WL = 1, C_NPAIRS = 2, C_CCOUNT = 3, C_NFREE = 4, C_ERR = 5, C_HFILL = 6, C_NHI = 7,
-       C_TL = 8, C_CHANGED = 9, C_TNP = 10, C_TNX = 11, C_TOTAL = 16 };
+       C_TL = 8, C_CHANGED = 9, C_TNP = 10, C_TNX = 11, C_R0 = 12, C_NEXT = 15, C_TOTAL = 16 };
 enum { ERR_CAP = 1, ERR_INTERNAL = 2 };
 
 __device__ __forceinline__ unsigned long long ev_key(long long t, int kind, int lo, int hi) {
@@ -85,9 +93,9 @@ __device__ __forceinline__ unsigned long long ev_key(long long t, int kind, int 
            ((unsigned long long)lo << 18) | (unsigned long long)hi;
 }
 
-// Loads of per-shot state written by other lanes of this warp (plain stores or
-// atomics): relaxed at CTA scope, so they may hit L1 and still observe every
-// write ordered before them by the warp's __syncwarp barriers.
+// Loads of per-shot state written by other threads of this team (plain stores
+// or atomics): relaxed at CTA scope, so they may hit L1 and still observe every
+// write ordered before them by the team's barriers.
 __device__ __forceinline__ int ldr(const int *p) {
     int v;
     asm volatile("ld.relaxed.cta.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -153,6 +161,174 @@ __device__ __forceinline__ long long warp_sum64(long long v) {
     for (int o = WS / 2; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
+
+__device__ __forceinline__ unsigned long long warp_xor64(unsigned long long v) {
+#pragma unroll
+    for (int o = WS / 2; o; o >>= 1) v ^= __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------ teams --
+
+// Shared scratch of a multi-warp team: one slot per warp for reductions, in
+// two alternating buffers (every team operation ends with one barrier, so a
+// buffer is reused only after every thread has read it).
+struct TeamShared {
+    unsigned long long u64[2][32];
+    int i32[2][32][2];
+};
+
+template <int NW>
+struct Team {
+    static constexpr int NT = WS * NW;
+    int tid;    // thread in the team, 0 .. NT - 1
+    int lane;   // lane in its warp
+    int warp;   // warp in the team, 0 .. NW - 1
+    int ph;     // buffer parity of the next team operation
+    TeamShared *sh;
+
+    __device__ __forceinline__ void sync() const {
+        if constexpr (NW == 1) __syncwarp(); else __syncthreads();
+    }
+    // thread 0's value for every thread
+    __device__ __forceinline__ int bcast(int v) {
+        if constexpr (NW == 1) {
+            return __shfl_sync(FULL, v, 0);
+        } else {
+            if (tid == 0) sh->i32[ph][0][0] = v;
+            __syncthreads();
+            v = sh->i32[ph][0][0];
+            ph ^= 1;
+            return v;
+        }
+    }
+    __device__ __forceinline__ unsigned long long bcast64(unsigned long long v) {
+        if constexpr (NW == 1) {
+            return __shfl_sync(FULL, v, 0);
+        } else {
+            if (tid == 0) sh->u64[ph][0] = v;
+            __syncthreads();
+            v = sh->u64[ph][0];
+            ph ^= 1;
+            return v;
+        }
+    }
+    __device__ __forceinline__ unsigned long long min64(unsigned long long v) {
+        v = warp_min64(v);
+        if constexpr (NW == 1) {
+            return v;
+        } else {
+            if (lane == 0) sh->u64[ph][warp] = v;
+            __syncthreads();
+            unsigned long long r = sh->u64[ph][0];
+            for (int w = 1; w < NW; w++) { const unsigned long long x = sh->u64[ph][w]; r = x < r ? x : r; }
+            ph ^= 1;
+            return r;
+        }
+    }
+    __device__ __forceinline__ long long sum64(long long v) {
+        v = warp_sum64(v);
+        if constexpr (NW == 1) {
+            return v;
+        } else {
+            if (lane == 0) sh->u64[ph][warp] = (unsigned long long)v;
+            __syncthreads();
+            long long r = 0;
+            for (int w = 0; w < NW; w++) r += (long long)sh->u64[ph][w];
+            ph ^= 1;
+            return r;
+        }
+    }
+    __device__ __forceinline__ unsigned long long xor64(unsigned long long v) {
+        v = warp_xor64(v);
+        if constexpr (NW == 1) {
+            return v;
+        } else {
+            if (lane == 0) sh->u64[ph][warp] = v;
+            __syncthreads();
+            unsigned long long r = 0;
+            for (int w = 0; w < NW; w++) r ^= sh->u64[ph][w];
+            ph ^= 1;
+            return r;
+        }
+    }
+    // op: 0 = add, 1 = max, 2 = or
+    template <int OP>
+    __device__ __forceinline__ int red32(int v) {
+        if constexpr (OP == 0) v = (int)__reduce_add_sync(FULL, (unsigned)v);
+        else if constexpr (OP == 1) v = __reduce_max_sync(FULL, v);
+        else v = (int)__reduce_or_sync(FULL, (unsigned)v);
+        if constexpr (NW == 1) {
+            return v;
+        } else {
+            if (lane == 0) sh->i32[ph][warp][0] = v;
+            __syncthreads();
+            int r = sh->i32[ph][0][0];
+            for (int w = 1; w < NW; w++) {
+                const int x = sh->i32[ph][w][0];
+                r = OP == 0 ? r + x : (OP == 1 ? (x > r ? x : r) : (r | x));
+            }
+            ph ^= 1;
+            return r;
+        }
+    }
+    __device__ __forceinline__ int add(int v) { return red32<0>(v); }
+    __device__ __forceinline__ int maxi(int v) { return red32<1>(v); }
+    __device__ __forceinline__ bool any(bool b) { return red32<2>(b ? 1 : 0) != 0; }
+    // The event search's reduction in one barrier: smallest key, OR of flags,
+    // smallest m (as unsigned).
+    __device__ __forceinline__ void reduce_ev(unsigned long long &key, int &flags, unsigned &m) {
+        key = warp_min64(key);
+        flags = (int)__reduce_or_sync(FULL, (unsigned)flags);
+        m = __reduce_min_sync(FULL, m);
+        if constexpr (NW > 1) {
+            if (lane == 0) {
+                sh->u64[ph][warp] = key;
+                sh->i32[ph][warp][0] = flags;
+                sh->i32[ph][warp][1] = (int)m;
+            }
+            __syncthreads();
+            key = sh->u64[ph][0];
+            flags = sh->i32[ph][0][0];
+            m = (unsigned)sh->i32[ph][0][1];
+            for (int w = 1; w < NW; w++) {
+                const unsigned long long x = sh->u64[ph][w];
+                key = x < key ? x : key;
+                flags |= sh->i32[ph][w][0];
+                const unsigned y = (unsigned)sh->i32[ph][w][1];
+                m = y < m ? y : m;
+            }
+            ph ^= 1;
+        }
+    }
+    // Exclusive prefix sum of v over the team's threads in tid order; `total`
+    // receives the sum over all threads.
+    __device__ __forceinline__ int excl_scan(int v, int &total) {
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < WS; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int wtot = __shfl_sync(FULL, incl, WS - 1);
+        if constexpr (NW == 1) {
+            total = wtot;
+            return incl - v;
+        } else {
+            if (lane == 0) sh->i32[ph][warp][0] = wtot;
+            __syncthreads();
+            int off = 0, tot = 0;
+            for (int w = 0; w < NW; w++) {
+                const int x = sh->i32[ph][w][0];
+                if (w < warp) off += x;
+                tot += x;
+            }
+            ph ^= 1;
+            total = tot;
+            return off + incl - v;
+        }
+    }
+};
 
 struct Slab {
     // per detection event (source)
@@ -363,28 +539,30 @@ __device__ __forceinline__ void bnd_update(const Slab &S, int s, int d, int eid)
     atomicMin(&S.sbnd[s], v);
 }
 
-__device__ __forceinline__ unsigned long long vs_pack(int v, int s) {
-    return ((unsigned long long)(unsigned)v << 32) | (unsigned)s;
-}
-
 // Grow the explored balls of the sources xsrc[0 .. nx) from radius sR[s] to
 // xR[i] (xR[i] - sR[s] >= largest weight), all at once: the previous band of
 // each source is the frontier, label-correcting relaxation runs on work lists
 // of table slots (a slot's key names the vertex and source, its value the
 // current distance) until no distance changes, every new entry is checked for
 // contacts with the other sources' balls, and each source's new band is stored
-// contiguously in `ent` as its next frontier.  All lanes call.
-__device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
+// contiguously in `ent` as its next frontier.  Every thread of the team calls
+// with the same nx.
+template <int NW>
+__device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
     const DGraph &g = C.g;
     if (nx <= 0) return;
-    __syncwarp();
-    if (lane == 0) { S.ctr[C_TL] = 0; S.ctr[C_WL] = 0; }
-    for (int i = lane; i < nx; i += WS) { S.xcnt[i] = 0; S.xidx[S.xsrc[i]] = i; }
-    __syncwarp();
+    const int lane = T.lane;
+    T.sync();
+    if (T.tid == 0) {
+        S.ctr[C_TL] = 0; S.ctr[C_WL] = 0;
+        if constexpr (NW > 1) { S.ctr[C_R0] = 0; S.ctr[C_R0 + 1] = 0; }
+    }
+    for (int i = T.tid; i < nx; i += T.NT) { S.xcnt[i] = 0; S.xidx[S.xsrc[i]] = i; }
+    T.sync();
     unsigned *F = reinterpret_cast<unsigned *>(S.wl0), *Wn = reinterpret_cast<unsigned *>(S.wl1);
     // initial frontier: the previous band of every listed source; a source
     // never explored so far starts from its own vertex at distance 0
-    for (int i = lane; i < nx; i += WS) {
+    for (int i = T.tid; i < nx; i += T.NT) {
         const int s = S.xsrc[i];
         if (S.sR[s] < 0) {
             unsigned hs;
@@ -405,19 +583,26 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
             else set_err(S, ERR_CAP);
         }
     }
-    __syncwarp();
+    T.sync();
     int nf = min(ldr(&S.ctr[C_WL]), C.wc);
-    // only this warp appends during the relaxation: the list counters live in
-    // registers (warp-uniform) and each round's appends are placed by ballot
+    // a one-warp team keeps the list counters in registers (warp-uniform) and
+    // places each round's appends by ballot; several warps reserve their
+    // appends with one atomic per warp and round on counters that rotate over
+    // three slots (a slot is cleared two rounds before its next use)
     int ntl = ldr(&S.ctr[C_TL]);
     const unsigned lt = (1u << lane) - 1u;
     for (int iter = 0;; iter++) {
-        if (iter >= 4096) { if (lane == 0) set_err(S, ERR_INTERNAL); break; }
+        if (iter >= 4096) { if (T.tid == 0) set_err(S, ERR_INTERNAL); break; }
         int nwl = 0;
+        int *const wctr = &S.ctr[C_R0 + iter % 3];
+        if constexpr (NW > 1) {
+            if (T.tid == 0) S.ctr[C_R0 + (iter + 1) % 3] = 0;
+        }
         // one lane per (work item, adjacency slot): items are taken 32 at a
-        // time, their slots numbered by a warp prefix sum of the degrees, and
-        // slot t goes to lane t mod 32 (its item found by binary search)
-        for (int base = 0; base < nf; base += WS) {
+        // time per warp, their slots numbered by a warp prefix sum of the
+        // degrees, and slot t goes to lane t mod 32 (its item found by binary
+        // search)
+        for (int base = T.warp * WS; base < nf; base += T.NT) {
             const int i = base + lane;
             unsigned long long key = 0;
             int dx = 0, Rn = -1, r0 = 0, deg = 0, xi = 0;
@@ -461,36 +646,64 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
                 }
                 const unsigned mt = __ballot_sync(FULL, r == 1);
                 const unsigned mw = __ballot_sync(FULL, r >= 1);
+                int bt, bw;
+                if constexpr (NW == 1) {
+                    bt = ntl; bw = nwl;
+                    ntl += __popc(mt);
+                    nwl += __popc(mw);
+                } else {
+                    bt = 0; bw = 0;
+                    if (lane == 0) {
+                        if (mt) bt = atomicAdd(&S.ctr[C_TL], __popc(mt));
+                        if (mw) bw = atomicAdd(wctr, __popc(mw));
+                    }
+                    bt = __shfl_sync(FULL, bt, 0);
+                    bw = __shfl_sync(FULL, bw, 0);
+                }
                 if (r == 1) {
-                    const int e = ntl + __popc(mt & lt);
+                    const int e = bt + __popc(mt & lt);
                     if (e < C.ec) S.tl[e] = ((unsigned long long)hs << 32) | (unsigned)oxi; else set_err(S, ERR_CAP);
                 }
                 if (r >= 1) {
-                    const int w = nwl + __popc(mw & lt);
+                    const int w = bw + __popc(mw & lt);
                     if (w < C.wc) Wn[w] = hs; else set_err(S, ERR_CAP);
                 }
-                ntl += __popc(mt);
-                nwl += __popc(mw);
             }
         }
-        __syncwarp();
+        T.sync();
+        if constexpr (NW > 1) nwl = ldr(wctr);
         const int err = ldr(&S.ctr[C_ERR]);
-        if (nwl == 0 || err) break;
+        bool stop = nwl == 0 || err;
+        if constexpr (NW > 1) stop = T.any(stop);
+        if (stop) break;
         nf = min(nwl, C.wc);
         unsigned *t = F; F = Wn; Wn = t;
     }
-    if (lane == 0) S.ctr[C_TL] = ntl;
-    __syncwarp();
-    const int nt = min(ldr(&S.ctr[C_TL]), C.ec);
-    const int e0 = ldr(&S.ctr[C_ECOUNT]);
+    if constexpr (NW == 1) {
+        if (lane == 0) S.ctr[C_TL] = ntl;
+    }
+    T.sync();
+    const int nt = T.bcast(min(ldr(&S.ctr[C_TL]), C.ec));
+    const int e0 = T.bcast(ldr(&S.ctr[C_ECOUNT]));
     // explored-entry table at most half full, list room left
-    if (e0 + nt > C.ec || (unsigned)(e0 + nt) * 2u > C.hmask) { if (lane == 0) set_err(S, ERR_CAP); __syncwarp(); return; }
+    if (e0 + nt > C.ec || (unsigned)(e0 + nt) * 2u > C.hmask) {
+        if (T.tid == 0) set_err(S, ERR_CAP);
+        T.sync();
+        return;
+    }
     // bands made contiguous per source (counting sort of the new entries)
-    for (int i = lane; i < nt; i += WS) atomicAdd(&S.xcnt[(int)(unsigned)(S.tl[i] & 0xffffffffu)], 1);
-    __syncwarp();
-    if (lane == 0) {
-        int acc = e0;
-        for (int i = 0; i < nx; i++) {
+    for (int i = T.tid; i < nt; i += T.NT) atomicAdd(&S.xcnt[(int)(unsigned)(S.tl[i] & 0xffffffffu)], 1);
+    T.sync();
+    {
+        // band starts: exclusive prefix sum of the counts in list order, each
+        // thread one contiguous chunk of the list
+        const int per = (nx + T.NT - 1) / T.NT;
+        const int i0 = min(nx, T.tid * per), i1 = min(nx, i0 + per);
+        int loc = 0;
+        for (int i = i0; i < i1; i++) loc += S.xcnt[i];
+        int total = 0;
+        int acc = e0 + T.excl_scan(loc, total);
+        for (int i = i0; i < i1; i++) {
             const int s = S.xsrc[i];
             const int c = S.xcnt[i];
             S.xcur[i] = acc;
@@ -500,15 +713,18 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
             if (c == 0) S.sexh[s] = 1;
             acc += c;
         }
-        S.ctr[C_ECOUNT] = acc;
+        if (T.tid == 0) {
+            S.ctr[C_ECOUNT] = e0 + total;
+            S.ctr[C_NEXT] = 0;
+        }
     }
-    __syncwarp();
-    for (int i = lane; i < nt; i += WS) {
+    T.sync();
+    for (int i = T.tid; i < nt; i += T.NT) {
         const unsigned long long it = S.tl[i];
         const int pos = atomicAdd(&S.xcur[(int)(unsigned)(it & 0xffffffffu)], 1);
         S.ent[pos] = (int)(it >> 32);
     }
-    __syncwarp();
+    T.sync();
     // contacts of every new entry y of source s: other explored balls holding y
     // (same vertex), and y being another detection event's own vertex (reach).
     // With explored radius >= Rad + L for every growing region (L >= largest
@@ -517,17 +733,26 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
     // between them, the first vertex at distance >= Rad(a) from a lies in b's
     // region and within Rad(a) + largest weight of a.
     // Each lane walks the probe chain of one entry, one probe per round; a lane
-    // whose walk has ended takes the next unwalked entry, so the warp's lanes
-    // stay busy however the chain lengths vary.
+    // whose walk has ended takes the next unwalked entry, so the lanes stay busy
+    // however the chain lengths vary (a warp of a larger team claims entries
+    // from a shared counter).
     {
-        const unsigned lt = (1u << lane) - 1u;
         int cur = -1, yv = 0, s = 0, dy = 0;
         unsigned pos = 0, nprobe = 0;
         int next = 0;
         for (long long round = 0; round < (long long)nt * (C.hmask + 2) + 1; round++) {
             const unsigned idle = __ballot_sync(FULL, cur < 0);
+            int kb;
+            if constexpr (NW == 1) {
+                kb = next;
+                next += __popc(idle);
+            } else {
+                kb = 0;
+                if (lane == 0 && idle) kb = atomicAdd(&S.ctr[C_NEXT], __popc(idle));
+                kb = __shfl_sync(FULL, kb, 0);
+            }
             if (cur < 0) {
-                const int k = next + __popc(idle & lt);
+                const int k = kb + __popc(idle & lt);
                 if (k < nt) {
                     cur = k;
                     const unsigned hy = (unsigned)(S.tl[k] >> 32);
@@ -543,7 +768,6 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
                     }
                 }
             }
-            next += __popc(idle);
             if (!__any_sync(FULL, cur >= 0)) break;
             if (cur >= 0) {
                 unsigned long long k;
@@ -561,14 +785,15 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, int lane) {
             }
         }
     }
-    __syncwarp();
+    T.sync();
 }
 
-// Grow one source's ball by one band.  All lanes call.
-__device__ void extend_one(const Slab &S, const Shot &C, int s, int lane) {
-    if (lane == 0) { S.xsrc[0] = s; S.xR[0] = max(S.sR[s], 0) + C.band; }
-    __syncwarp();
-    extend_many(S, C, 1, lane);
+// Grow one source's ball by one band.  Every thread of the team calls.
+template <int NW>
+__device__ void extend_one(const Slab &S, const Shot &C, int s, Team<NW> &T) {
+    if (T.tid == 0) { S.xsrc[0] = s; S.xR[0] = max(S.sR[s], 0) + C.band; }
+    T.sync();
+    extend_many(S, C, 1, T);
 }
 
 // ---------------------------------------------------------------- matcher --
@@ -580,7 +805,7 @@ __device__ __forceinline__ int child_of(const Slab &S, int B, int leaf) {
     return v;
 }
 
-// flip matches along the tree path from outer A to its root (lane 0)
+// flip matches along the tree path from outer A to its root (thread 0)
 __device__ void flip_to_root(const Slab &S, int A) {
     int v = A;
     for (int n = 0; n < 1 << 22 && S.tpar[v] >= 0; n++) {
@@ -593,10 +818,11 @@ __device__ void flip_to_root(const Slab &S, int A) {
     }
 }
 
-// Events (b), (f), (g).  B < 0: boundary.  All lanes call.
-__device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, int B, int b, int lane, int nhi) {
+// Events (b), (f), (g).  B < 0: boundary.  Every thread of the team calls.
+template <int NW>
+__device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, int B, int b, Team<NW> &T, int nhi) {
     int rA = 0, rB = -3;
-    if (lane == 0) {
+    if (T.tid == 0) {
         rA = S.nroot[A];
         const bool bout = B >= 0 && S.label[B] == 1;
         rB = bout ? S.nroot[B] : -3;
@@ -609,28 +835,29 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
             S.mate[A] = MATE_BOUNDARY; S.ms[A] = a; S.mo[A] = -1;
         }
     }
-    rA = __shfl_sync(FULL, rA, 0);
-    rB = __shfl_sync(FULL, rB, 0);
-    __syncwarp();
-    for (int v = lane; v < nhi; v += WS) {
+    rA = T.bcast(rA);
+    rB = T.bcast(rB);
+    T.sync();
+    for (int v = T.tid; v < nhi; v += T.NT) {
         if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0 && (S.nroot[v] == rA || S.nroot[v] == rB)) {
             S.label[v] = 0; S.tpar[v] = -1; S.nroot[v] = -1;
         }
     }
-    __syncwarp();
+    T.sync();
 }
 
-// Event (a): outer A touches frozen B (matched to C).  Lane 0 only.
+// Event (a): outer A touches frozen B (matched to C).  Thread 0 only.
 __device__ void ev_grow(const Slab &S, int A, int a, int B, int b) {
     const int Cn = S.mate[B];
     S.label[B] = -1; S.tpar[B] = A; S.tps[B] = b; S.tpo[B] = a; S.nroot[B] = S.nroot[A];
     S.label[Cn] = 1; S.tpar[Cn] = B; S.tps[Cn] = S.ms[Cn]; S.tpo[Cn] = S.mo[Cn]; S.nroot[Cn] = S.nroot[A];
 }
 
-// Event (c): outer A, B in one tree form a blossom.  All lanes call.
-__device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, int B, int b, int lane, int &nhi) {
+// Event (c): outer A, B in one tree form a blossom.  Every thread of the team calls.
+template <int NW>
+__device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, int B, int b, Team<NW> &T, int &nhi) {
     int N = -1, L = -1, Lroot = 0;
-    if (lane == 0) {
+    if (T.tid == 0) {
         int na = 0, nb = 0;
         for (int v = A; v >= 0 && na < 2 * C.nc; v = S.tpar[v]) S.tmpa[na++] = v;
         for (int v = B; v >= 0 && nb < 2 * C.nc; v = S.tpar[v]) S.tmpb[nb++] = v;
@@ -667,13 +894,13 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
             for (int j = 0; j < m; j++) S.bpar[S.cnode[cb + j]] = N;
         }
     }
-    N = __shfl_sync(FULL, N, 0);
-    L = __shfl_sync(FULL, L, 0);
-    Lroot = __shfl_sync(FULL, Lroot, 0);
-    __syncwarp();
+    N = T.bcast(N);
+    L = T.bcast(L);
+    Lroot = T.bcast(Lroot);
+    T.sync();
     if (N < 0) return;
     nhi = max(nhi, N + 1);
-    for (int v = lane; v < nhi; v += WS) {
+    for (int v = T.tid; v < nhi; v += T.NT) {
         if (!S.alive[v] || S.bpar[v] >= 0 || v == N) continue;
         const int tp = S.tpar[v];
         if (tp >= 0 && S.bpar[tp] == N) S.tpar[v] = N;
@@ -681,22 +908,23 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
         if (mt >= 0 && S.bpar[mt] == N) S.mate[v] = N;
         if (Lroot && S.nroot[v] == L) S.nroot[v] = N;
     }
-    for (int s = lane; s < C.K; s += WS) {
+    for (int s = T.tid; s < C.K; s += T.NT) {
         const int tp = S.stop[s];
         if (tp != N && S.bpar[tp] == N) S.stop[s] = N;
     }
-    __syncwarp();
+    T.sync();
 }
 
-// Event (d): inner blossom B with zero dual shatters.  All lanes call.
-__device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, int lane) {
-    for (int s = lane; s < C.K; s += WS)
+// Event (d): inner blossom B with zero dual shatters.  Every thread of the team calls.
+template <int NW>
+__device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> &T) {
+    for (int s = T.tid; s < C.K; s += T.NT)
         if (S.stop[s] == B) {
             const int c = child_of(S, B, s);
             if (c >= 0) S.stop[s] = c; else atomicOr(&S.ctr[C_ERR], ERR_INTERNAL);
         }
-    __syncwarp();
-    if (lane == 0) {
+    T.sync();
+    if (T.tid == 0) {
         const int m = S.clen[B], cb = S.cbeg[B];
         const int P = S.tpar[B], Cn = S.mate[B];
         const int xp = S.tps[B] >= 0 ? child_of(S, B, S.tps[B]) : -1;
@@ -758,7 +986,7 @@ __device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, int lane)
             S.ctr[C_NFREE] = nf + 1;
         }
     }
-    __syncwarp();
+    T.sync();
 }
 
 // Fresh growing root for source s.
@@ -770,26 +998,27 @@ __device__ __forceinline__ void make_root(const Slab &S, int s) {
 enum { RUN_OK = 0, RUN_NOSOL = 1, RUN_BUDGET = 2, RUN_CAP = 3, RUN_INTERNAL = 4 };
 
 // Event loop over the sources with inplay[s] = 1, from t = 0 (SI S1).
-__device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
+template <int NW>
+__device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
     C.t = 0;
     for (;;) {
         if (++C.events > C.max_events) return RUN_BUDGET;
         if (C.deadline && (C.events & 63) == 0) {
-            bool late = false;
-            if (lane == 0) late = now_ns() > C.deadline;
-            if (__shfl_sync(FULL, late, 0)) return RUN_BUDGET;
+            int late = 0;
+            if (T.tid == 0) late = now_ns() > C.deadline;
+            if (T.bcast(late)) return RUN_BUDGET;
         }
         unsigned long long best = EMPTY64;
-        bool outer = false, bad = false;
-        int inner_leaf_min = INT_MAX;
-        for (int s = lane; s < C.K; s += WS) {
+        int flags = 0;   // bit 0: a growing region exists, bit 1: inconsistent state
+        unsigned inner_leaf_min = INT_MAX;
+        for (int s = T.tid; s < C.K; s += T.NT) {
             // independent loads first, one dependent load (the label) after
             const int ip = S.inplay[s], A = S.stop[s], rad = S.srad[s], exh = S.sexh[s], sR = S.sR[s];
             const unsigned long long bb = ldr(&S.sbnd[s]);
             if (!ip) continue;
             const int lab = S.label[A];
             if (lab == 1) {
-                outer = true;
+                flags |= 1;
                 if (!exh) {
                     // due when Rad(s) + L would pass the explored radius; a region that
                     // just started growing (or was never explored) is due at once
@@ -798,15 +1027,15 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
                 }
                 if (bb != EMPTY64) {
                     const int bd = (int)(bb >> 32);
-                    if (bd < rad) bad = true;
+                    if (bd < rad) flags |= 2;
                     else best = min(best, ev_key(C.t + (bd - rad), EV_BOUNDARY, s, ID_MAX));
                 }
             } else if (lab == -1 && A == s) {
-                inner_leaf_min = min(inner_leaf_min, S.y[s]);
+                inner_leaf_min = min(inner_leaf_min, (unsigned)S.y[s]);
             }
         }
         const int np = ldr(&S.ctr[C_NPAIRS]);
-        for (int i = lane; i < np; i += WS) {
+        for (int i = T.tid; i < np; i += T.NT) {
             const int sl = S.plist[i];
             unsigned long long k;
             int pv;
@@ -818,19 +1047,16 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
             const int r = S.label[A] + S.label[B];
             if (r <= 0) continue;
             const int gap = pv - ra - rb;
-            if (gap < 0 || gap % r) { bad = true; continue; }
+            if (gap < 0 || gap % r) { flags |= 2; continue; }
             best = min(best, ev_key(C.t + gap / r, EV_COLLIDE, a, b));
         }
-        for (int v = C.K + lane; v < nhi; v += WS) {
+        for (int v = C.K + T.tid; v < nhi; v += T.NT) {
             if (S.alive[v] && S.bpar[v] < 0 && S.label[v] == -1)
                 best = min(best, ev_key(C.t + S.y[v], EV_IMPLODE, S.minleaf[v], 0));
         }
-        best = warp_min64(best);
-        outer = __any_sync(FULL, outer);
-        bad = __any_sync(FULL, bad);
-        inner_leaf_min = __reduce_min_sync(FULL, (unsigned)inner_leaf_min);
-        if (bad) return RUN_INTERNAL;
-        if (!outer) return RUN_OK;
+        T.reduce_ev(best, flags, inner_leaf_min);
+        if (flags & 2) return RUN_INTERNAL;
+        if (!(flags & 1)) return RUN_OK;
         if (best == EMPTY64) return RUN_NOSOL;
         const long long tn = (long long)(best >> 38);
         const int kind = (int)((best >> 36) & 3);
@@ -838,11 +1064,11 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
         const int hi = (int)(best & ID_MAX);
         if (tn >= T_MAX) return RUN_CAP;
         const int dt = (int)(tn - C.t);
-        if (dt > inner_leaf_min) return RUN_INTERNAL;
+        if ((unsigned)dt > inner_leaf_min) return RUN_INTERNAL;
         if (dt > 0) {
-            for (int v = lane; v < nhi; v += WS)
+            for (int v = T.tid; v < nhi; v += T.NT)
                 if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0) S.y[v] += S.label[v] * dt;
-            for (int s = lane; s < C.K; s += WS)
+            for (int s = T.tid; s < C.K; s += T.NT)
                 if (S.inplay[s]) S.srad[s] += S.label[S.stop[s]] * dt;
         }
         C.t = tn;
@@ -853,12 +1079,12 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
             if (tn <= C.tcut) C.ncut++;
             C.tlast = (int)tn;
         }
-        __syncwarp();
+        T.sync();
         if (kind == EV_EXTEND) {
             // every growing region that reached its explored radius now
-            if (lane == 0) S.ctr[C_WL] = 0;
-            __syncwarp();
-            for (int s = lane; s < C.K; s += WS) {
+            if (T.tid == 0) S.ctr[C_WL] = 0;
+            T.sync();
+            for (int s = T.tid; s < C.K; s += T.NT) {
                 const int rad = S.srad[s];
                 if (S.inplay[s] && !S.sexh[s] && S.label[S.stop[s]] == 1 && S.sR[s] - C.L + 1 - rad <= 0) {
                     const int k = atomicAdd(&S.ctr[C_WL], 1);
@@ -866,89 +1092,106 @@ __device__ int run_matcher(const Slab &S, Shot &C, int lane, int &nhi) {
                     S.xR[k] = max(S.sR[s] + C.band, rad + C.L + C.band);
                 }
             }
-            __syncwarp();
-            extend_many(S, C, ldr(&S.ctr[C_WL]), lane);
+            T.sync();
+            extend_many(S, C, T.bcast(ldr(&S.ctr[C_WL])), T);
         } else if (kind == EV_IMPLODE) {
-            ev_shatter(S, C, S.stop[lo], lane);
+            ev_shatter(S, C, S.stop[lo], T);
         } else if (kind == EV_BOUNDARY) {
-            ev_augment(S, C, S.stop[lo], lo, -1, -1, lane, nhi);
+            ev_augment(S, C, S.stop[lo], lo, -1, -1, T, nhi);
         } else {
             int a = lo, b = hi;
             int A = S.stop[a], B = S.stop[b];
             if (S.label[A] != 1) { int t = A; A = B; B = t; t = a; a = b; b = t; }
             const int lb = S.label[B];
-            if (lb == 1) {
-                if (S.nroot[A] == S.nroot[B]) ev_blossom(S, C, A, a, B, b, lane, nhi);
-                else ev_augment(S, C, A, a, B, b, lane, nhi);
-            } else if (lb == 0 && S.mate[B] == MATE_BOUNDARY) {
-                ev_augment(S, C, A, a, B, b, lane, nhi);
-            } else if (lb == 0 && S.mate[B] >= 0) {
-                if (lane == 0) ev_grow(S, A, a, B, b);
-                __syncwarp();
+            // 0 blossom, 1 augment, 2 grow, 3 inconsistent
+            int act = 3;
+            if (lb == 1) act = S.nroot[A] == S.nroot[B] ? 0 : 1;
+            else if (lb == 0 && S.mate[B] == MATE_BOUNDARY) act = 1;
+            else if (lb == 0 && S.mate[B] >= 0) act = 2;
+            // every thread has read the state it dispatches on before any
+            // thread changes it
+            if constexpr (NW > 1) T.sync();
+            if (act == 0) ev_blossom(S, C, A, a, B, b, T, nhi);
+            else if (act == 1) ev_augment(S, C, A, a, B, b, T, nhi);
+            else if (act == 2) {
+                if (T.tid == 0) ev_grow(S, A, a, B, b);
+                T.sync();
             } else {
                 return RUN_INTERNAL;
             }
         }
+        // the error word is written only before the barrier that ends each
+        // step above and after the next event search's barrier, so every
+        // thread reads the same value here
         const int err = ldr(&S.ctr[C_ERR]);
         if (err) return (err & ERR_INTERNAL) ? RUN_INTERNAL : RUN_CAP;
     }
 }
 
 // Canonical path observable from source s (its Dijkstra tree) to vertex x at
-// distance dx: predecessor = lowest edge id among tight edges.  All lanes call.
-__device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int dx, int lane) {
+// distance dx: predecessor = lowest edge id among tight edges.  Every thread
+// of the team calls.
+template <int NW>
+__device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int dx, Team<NW> &T) {
     const DGraph &g = C.g;
-    for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]); n++) extend_one(S, C, s, lane);
+    for (int n = 0; n < 1 << 16; n++) {
+        const int more = S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]);
+        if (!T.bcast(more)) break;
+        extend_one(S, C, s, T);
+    }
     // a ball that outgrew the tables: the attempt is retried with larger ones
-    if (ldr(&S.ctr[C_ERR])) return 0;
+    if (T.bcast(ldr(&S.ctr[C_ERR]))) return 0;
     unsigned long long o = 0;
     const int src = S.svtx[s];
     int cur = x, dcur = dx;
     for (int n = 0; n < 1 << 22 && cur != src; n++) {
         const int r0 = __ldg(g.row + cur), r1 = __ldg(g.row + cur + 1);
         unsigned long long best = EMPTY64;
-        for (int j = r0 + lane; j < r1; j += WS) {
+        for (int j = r0 + T.tid; j < r1; j += T.NT) {
             SlotV sl = load_slot(g, j);
             if (sl.nbr < 0) continue;
             const int dy = ht_get(S, C, sl.nbr, s);
             if (dy != INF32 && dy + sl.w == dcur)
                 best = min(best, ((unsigned long long)(unsigned)__ldg(g.seid + j) << 32) | (unsigned)sl.nbr);
         }
-        best = warp_min64(best);
-        if (best == EMPTY64) { if (lane == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
+        best = T.min64(best);
+        if (best == EMPTY64) { if (T.tid == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
         const int e = (int)(best >> 32);
         o ^= __ldg(g.eobs + e);
         cur = (int)(unsigned)(best & 0xffffffffu);
         dcur = ht_get(S, C, cur, s);
     }
+    T.sync();
     return o;
 }
 
 // Expand the final matching into leaf-level pairs (tmpa[i], tmpb[i]; tmpb = -1
 // for a boundary match) and accumulate weight (internal units) and obs.
-__device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, long long &wint, unsigned long long &obs) {
-    // matched top-level nodes, lane-parallel: each match appends its leaf pair
+template <int NW>
+__device__ __noinline__ void trace(const Slab &S, Shot &C, Team<NW> &T, int nhi, long long &wint,
+                                   unsigned long long &obs) {
+    // matched top-level nodes, team-parallel: each match appends its leaf pair
     // and queues the blossoms on either side for expansion (stack seeds)
-    if (lane == 0) { S.ctr[C_TNP] = 0; S.ctr[C_TNX] = 0; }
-    __syncwarp();
+    if (T.tid == 0) { S.ctr[C_TNP] = 0; S.ctr[C_TNX] = 0; }
+    T.sync();
     int *stk = S.stk;
-    for (int v = lane; v < nhi; v += WS) {
+    for (int v = T.tid; v < nhi; v += T.NT) {
         if (!S.alive[v] || S.bpar[v] >= 0) continue;
         const int mt = S.mate[v];
         if (mt == MATE_BOUNDARY) {
-            const int k = agg_inc(&S.ctr[C_TNP], lane);
+            const int k = agg_inc(&S.ctr[C_TNP], T.lane);
             S.tmpa[k] = S.ms[v]; S.tmpb[k] = -1;
             if (v >= C.K) { const int x = atomicAdd(&S.ctr[C_TNX], 1); stk[2 * x] = v; stk[2 * x + 1] = S.ms[v]; }
         } else if (mt >= 0 && v < mt) {
-            const int k = agg_inc(&S.ctr[C_TNP], lane);
+            const int k = agg_inc(&S.ctr[C_TNP], T.lane);
             S.tmpa[k] = S.ms[v]; S.tmpb[k] = S.mo[v];
             if (v >= C.K) { const int x = atomicAdd(&S.ctr[C_TNX], 1); stk[2 * x] = v; stk[2 * x + 1] = S.ms[v]; }
             if (mt >= C.K) { const int x = atomicAdd(&S.ctr[C_TNX], 1); stk[2 * x] = mt; stk[2 * x + 1] = S.mo[v]; }
         }
     }
-    __syncwarp();
+    T.sync();
     int np = ldr(&S.ctr[C_TNP]);
-    if (lane == 0) {
+    if (T.tid == 0) {
         // blossoms: the child holding the externally matched leaf keeps that
         // match, the other children pair up along the cycle
         const int stk_cap = 4 * C.nc + 60;
@@ -973,12 +1216,12 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, lo
             }
         }
     }
-    np = __shfl_sync(FULL, np, 0);
-    __syncwarp();
-    if (lane == 0) S.ctr[C_TNP] = np;   // leaf pairs in tmpa / tmpb, read by commit_trace
+    np = T.bcast(np);
+    T.sync();
+    if (T.tid == 0) S.ctr[C_TNP] = np;   // leaf pairs in tmpa / tmpb, read by commit_trace
     long long w = 0;
     unsigned long long o = 0;
-    for (int i = lane; i < np; i += WS) {
+    for (int i = T.tid; i < np; i += T.NT) {
         const int a = S.tmpa[i], b = S.tmpb[i];
         if (a < 0 || a >= C.K || b >= C.K) { set_err(S, ERR_INTERNAL); continue; }
         if (b < 0) {
@@ -992,10 +1235,9 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, lo
             w += d;
         }
     }
-    w = warp_sum64(w);
-#pragma unroll
-    for (int off = WS / 2; off; off >>= 1) o ^= __shfl_xor_sync(FULL, o, off);
-    if (C.g.internal_obs && !ldr(&S.ctr[C_ERR])) {
+    w = T.sum64(w);
+    o = T.xor64(o);
+    if (C.g.internal_obs && !T.bcast(ldr(&S.ctr[C_ERR]))) {
         // detector-detector edges carry observables: walk the canonical paths
         for (int i = 0; i < np; i++) {
             const int a = S.tmpa[i], b = S.tmpb[i];
@@ -1003,10 +1245,10 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, int lane, int nhi, lo
                 const unsigned long long bb = ldr(&S.sbnd[a]);
                 const int e = (int)(unsigned)(bb & 0xffffffffu);
                 const int2 ue = __ldg(C.g.eend + e);
-                o ^= path_obs(S, C, a, ue.x, (int)(bb >> 32) - ue.y, lane);
+                o ^= path_obs(S, C, a, ue.x, (int)(bb >> 32) - ue.y, T);
             } else {
                 const int lo = min(a, b), hi = max(a, b);
-                o ^= path_obs(S, C, lo, S.svtx[hi], pair_get(S, C, lo, hi), lane);
+                o ^= path_obs(S, C, lo, S.svtx[hi], pair_get(S, C, lo, hi), T);
             }
         }
     }
@@ -1021,33 +1263,39 @@ __device__ __forceinline__ bool in_commit(const DGraph &g, int v) {
 // Canonical path from source s's vertex to vertex x at distance dx (the path
 // of path_obs): the XOR of the observables of its edges that touch the commit
 // region; each such edge with its other endpoint outside the region flips that
-// endpoint in `carry` (lane 0 writes).  All lanes call.
-__device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, int dx, int lane, unsigned *carry) {
+// endpoint in `carry` (thread 0 writes).  Every thread of the team calls.
+template <int NW>
+__device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, int dx, Team<NW> &T,
+                                          unsigned *carry) {
     const DGraph &g = C.g;
-    for (int n = 0; n < 1 << 16 && S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]); n++) extend_one(S, C, s, lane);
+    for (int n = 0; n < 1 << 16; n++) {
+        const int more = S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]);
+        if (!T.bcast(more)) break;
+        extend_one(S, C, s, T);
+    }
     // a ball that outgrew the tables: the attempt is retried with larger ones
-    if (ldr(&S.ctr[C_ERR])) return 0;
+    if (T.bcast(ldr(&S.ctr[C_ERR]))) return 0;
     unsigned long long o = 0;
     const int src = S.svtx[s];
     int cur = x, dcur = dx;
     for (int n = 0; n < 1 << 22 && cur != src; n++) {
         const int r0 = __ldg(g.row + cur), r1 = __ldg(g.row + cur + 1);
         unsigned long long best = EMPTY64;
-        for (int j = r0 + lane; j < r1; j += WS) {
+        for (int j = r0 + T.tid; j < r1; j += T.NT) {
             SlotV sl = load_slot(g, j);
             if (sl.nbr < 0) continue;
             const int dy = ht_get(S, C, sl.nbr, s);
             if (dy != INF32 && dy + sl.w == dcur)
                 best = min(best, ((unsigned long long)(unsigned)__ldg(g.seid + j) << 32) | (unsigned)sl.nbr);
         }
-        best = warp_min64(best);
-        if (best == EMPTY64) { if (lane == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
+        best = T.min64(best);
+        if (best == EMPTY64) { if (T.tid == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
         const int e = (int)(best >> 32);
         const int nxt = (int)(unsigned)(best & 0xffffffffu);
         const bool ci = in_commit(g, cur), ni = in_commit(g, nxt);
         if (ci || ni) {
             o ^= __ldg(g.eobs + e);
-            if (ci != ni && lane == 0) {
+            if (ci != ni && T.tid == 0) {
                 const int out = ci ? nxt : cur;
                 carry[out >> 5] ^= 1u << (out & 31);
             }
@@ -1055,6 +1303,7 @@ __device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, 
         cur = nxt;
         dcur = ht_get(S, C, cur, s);
     }
+    T.sync();
     return o;
 }
 
@@ -1062,51 +1311,56 @@ __device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, 
 // correction is the union of the canonical matching paths (and boundary
 // edges); every edge that touches the graph's commit region is committed.
 // Returns the committed observable; the shot's carry row receives the
-// detectors outside the region flipped by committed edges.  All lanes call.
-__device__ __noinline__ unsigned long long commit_trace(const Slab &S, Shot &C, int lane, unsigned *carry) {
+// detectors outside the region flipped by committed edges.  Every thread of
+// the team calls.
+template <int NW>
+__device__ __noinline__ unsigned long long commit_trace(const Slab &S, Shot &C, Team<NW> &T, unsigned *carry) {
     const DGraph &g = C.g;
-    for (int w = lane; w < g.words; w += WS) carry[w] = 0u;
-    __syncwarp();
-    const int np = ldr(&S.ctr[C_TNP]);
+    for (int w = T.tid; w < g.words; w += T.NT) carry[w] = 0u;
+    T.sync();
+    const int np = T.bcast(ldr(&S.ctr[C_TNP]));
     unsigned long long o = 0;
-    for (int i = 0; i < np && !ldr(&S.ctr[C_ERR]); i++) {
+    for (int i = 0; i < np; i++) {
+        if (T.bcast(ldr(&S.ctr[C_ERR]))) break;
         const int a = S.tmpa[i], b = S.tmpb[i];
         if (b < 0) {
             const unsigned long long bb = ldr(&S.sbnd[a]);
             const int e = (int)(unsigned)(bb & 0xffffffffu);
             const int2 ue = __ldg(g.eend + e);
             if (in_commit(g, ue.x)) o ^= __ldg(g.eobs + e);   // the boundary edge itself
-            o ^= path_commit(S, C, a, ue.x, (int)(bb >> 32) - ue.y, lane, carry);
+            o ^= path_commit(S, C, a, ue.x, (int)(bb >> 32) - ue.y, T, carry);
         } else {
             const int lo = min(a, b), hi = max(a, b);
-            o ^= path_commit(S, C, lo, S.svtx[hi], pair_get(S, C, lo, hi), lane, carry);
+            o ^= path_commit(S, C, lo, S.svtx[hi], pair_get(S, C, lo, hi), T, carry);
         }
     }
-    __syncwarp();
+    T.sync();
     return o;
 }
 
 // Per-shot counters; the tables themselves are already empty (release_tables).
-__device__ void clear_tables(const Slab &S, const Shot &C, int lane) {
-    for (int i = lane; i < C_TOTAL; i += WS) S.ctr[i] = 0;
-    __syncwarp();
+template <int NW>
+__device__ void clear_tables(const Slab &S, const Shot &C, Team<NW> &T) {
+    for (int i = T.tid; i < C_TOTAL; i += T.NT) S.ctr[i] = 0;
+    T.sync();
 }
 
 // Return the explored and pair tables to empty: the slots recorded in the band
 // lists (every explored entry) and the pair list (every pair), or with `all`
 // the whole region of this attempt's table sizes.
-__device__ __noinline__ void release_tables(const Slab &S, const Shot &C, int lane, bool all) {
-    __syncwarp();
+template <int NW>
+__device__ __noinline__ void release_tables(const Slab &S, const Shot &C, Team<NW> &T, bool all) {
+    T.sync();
     const HEnt e = HEnt{EMPTY64, -1, -1};
     if (all) {
-        for (unsigned i = lane; i <= C.hmask; i += WS) S.ht[i] = e;
-        for (unsigned i = lane; i <= C.pmask; i += WS) S.pt[i] = e;
+        for (unsigned i = T.tid; i <= C.hmask; i += T.NT) S.ht[i] = e;
+        for (unsigned i = T.tid; i <= C.pmask; i += T.NT) S.pt[i] = e;
     } else {
         const int ne = ldr(&S.ctr[C_ECOUNT]), np = ldr(&S.ctr[C_NPAIRS]);
-        for (int i = lane; i < ne; i += WS) S.ht[S.ent[i] & C.hmask] = e;
-        for (int i = lane; i < np; i += WS) S.pt[S.plist[i] & C.pmask] = e;
+        for (int i = T.tid; i < ne; i += T.NT) S.ht[S.ent[i] & C.hmask] = e;
+        for (int i = T.tid; i < np; i += T.NT) S.pt[S.plist[i] & C.pmask] = e;
     }
-    __syncwarp();
+    T.sync();
 }
 
 __device__ __forceinline__ unsigned next_pow2(unsigned x) {
@@ -1115,7 +1369,7 @@ __device__ __forceinline__ unsigned next_pow2(unsigned x) {
 }
 
 // Compact the set bits of the shot's syndrome row into S.svtx; returns K
-// (or -1 when K exceeds kcap).
+// (or -1 when K exceeds kcap).  One warp.
 __device__ int load_defects(const Slab &S, const DGraph &g, const unsigned *row, int kcap, int wcap, int lane) {
     int K = 0;
     const int nvec = g.words >> 2;
@@ -1227,10 +1481,13 @@ __device__ __noinline__ int local_ball(const Slab &S, const Shot &C, int s, int 
 // canonical boundary contact whenever it lies within Rb / 2 (a longer contact
 // is only an upper bound, refined by the flooder before a region can reach
 // it).  One lane per (event, adjacency slot of the event), numbered by a warp
-// prefix sum of the degrees.  All lanes call.
-__device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, int lane) {
+// prefix sum of the degrees; the warps of a team take 32 events each in turn.
+// Every thread of the team calls (no team barrier inside).
+template <int NW>
+__device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, const Team<NW> &T) {
     const DGraph &g = C.g;
-    for (int base = 0; base < C.K; base += WS) {
+    const int lane = T.lane;
+    for (int base = T.warp * WS; base < C.K; base += T.NT) {
         const int s = base + lane;
         int src = -1, r0 = 0, deg = 0;
         if (s < C.K) {
@@ -1289,9 +1546,9 @@ __device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, i
 // when the working set overflowed (retry with a larger scale).
 // WIN: sliding-window mode (BatchArgs::carry set), compiled as its own kernel so
 // that the ordinary kernel carries none of its code.
-template <bool WIN>
+template <bool WIN, int NW>
 __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
-                                   int lane, unsigned scale, unsigned long long deadline, long long &w_out,
+                                   Team<NW> &T, unsigned scale, unsigned long long deadline, long long &w_out,
                                    unsigned long long &o_out, int *dg, Shot &C) {
     C.g = g;
     C.ec = A.caps.ec; C.wc = A.caps.wc; C.cc = A.caps.cc;
@@ -1303,15 +1560,18 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     C.L = max(g.wmax, (g.b1 + 1) / 2) + 1;
     C.nm = 0; C.ncut = 0; C.tcut = 0; C.tlast = 0; C.nx = 0;
     if (g.words > A.caps.wcap) return -2;
-    const int K = load_defects(S, g, row, A.caps.kc, A.caps.wcap, lane);
+    int K = 0;
+    if (T.warp == 0) K = load_defects(S, g, row, A.caps.kc, A.caps.wcap, T.lane);
+    K = T.bcast(K);
+    T.sync();
     if (K < 0) return -2;
     C.K = K;
     C.max_events = min(A.max_events, 256LL * K + 4096);
     if (K == 0) {
         w_out = 0; o_out = 0;
-        if (dg && lane < QEC_DIAG_FIELDS) dg[lane] = 0;   // no detection event: E_ideal = 0
+        if (dg && T.tid < QEC_DIAG_FIELDS) dg[T.tid] = 0;   // no detection event: E_ideal = 0
         if constexpr (WIN)
-            for (int w = lane; w < g.words; w += WS) A.carry[(row - A.syn) + w] = 0u;
+            for (int w = T.tid; w < g.words; w += T.NT) A.carry[(row - A.syn) + w] = 0u;
         return QEC_SHOT_OK;
     }
     if (K > ID_MAX - 1 || 2 * K + 8 > A.caps.nc) return -2;
@@ -1323,23 +1583,23 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     const unsigned ps = min(next_pow2(max(64u, 4u * (unsigned)K * scale)), (unsigned)A.caps.phc);
     C.hmask = hs - 1;
     C.pmask = ps - 1;
-    clear_tables(S, C, lane);
+    clear_tables(S, C, T);
     // sources, leaf nodes, free list
     int nhi = K;
-    for (int s = lane; s < K; s += WS) {
+    for (int s = T.tid; s < K; s += T.NT) {
         S.srad[s] = 0; S.sR[s] = -1; S.scnt[s] = 0; S.sbeg[s] = 0; S.sexh[s] = 0; S.inplay[s] = 0;
         S.sbnd[s] = EMPTY64;
         S.alive[s] = 0; S.y[s] = 0; S.bpar[s] = -1; S.label[s] = 0; S.tpar[s] = -1;
         S.mate[s] = MATE_NONE; S.nroot[s] = -1; S.stop[s] = s; S.minleaf[s] = s; S.clen[s] = 0;
     }
     const int nfree = C.nc - K;
-    for (int i = lane; i < nfree; i += WS) {
+    for (int i = T.tid; i < nfree; i += T.NT) {
         const int v = C.nc - 1 - i;   // pop order: K, K+1, ...
         S.freel[i] = v;
         S.alive[v] = 0; S.clen[v] = 0; S.bpar[v] = -1;
     }
-    if (lane == 0) { S.ctr[C_ECOUNT] = 0; S.ctr[C_NFREE] = nfree; }
-    __syncwarp();
+    if (T.tid == 0) { S.ctr[C_ECOUNT] = 0; S.ctr[C_NFREE] = nfree; }
+    T.sync();
     // level-1 critical path (stopping time, event count), clusters, events
     // resolved at level 1, events of all level-1 runs
     int t1 = 0, e1 = 0, ncl1 = 0, nres1 = 0, ntot = 0;
@@ -1349,38 +1609,38 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         // lane-local Dijkstra (each lane its own events): pairs within b_1 with their
         // exact distance (found by reaching the other event's vertex) and the
         // canonical boundary candidate.  Events whose neighbourhood is too large for
-        // the lane go through the warp-wide flooder instead.
+        // the lane go through the team-wide flooder instead.
         bool any_big = false;
         if (g.hop2) {
-            level1_2hop(S, C, g.b1, lane);
+            level1_2hop(S, C, g.b1, T);
         } else {
-            for (int s = lane; s < K; s += WS) {
+            for (int s = T.tid; s < K; s += T.NT) {
                 const int r = local_ball(S, C, s, g.b1);
                 if (r < 0) { S.cst0[s] = 1; any_big = true; } else S.cst0[s] = 0;
             }
         }
-        __syncwarp();
-        if (__any_sync(FULL, any_big)) {
-            if (lane == 0) {
+        T.sync();
+        if (T.any(any_big)) {
+            if (T.tid == 0) {
                 int k = 0;
                 for (int s = 0; s < K; s++)
                     if (S.cst0[s]) { S.xsrc[k] = s; S.xR[k] = max(g.b1, C.band); k++; }
                 S.ctr[C_WL] = k;
             }
-            __syncwarp();
-            extend_many(S, C, ldr(&S.ctr[C_WL]), lane);
+            T.sync();
+            extend_many(S, C, T.bcast(ldr(&S.ctr[C_WL])), T);
         }
         {
-            const int err = ldr(&S.ctr[C_ERR]);
+            const int err = T.bcast(ldr(&S.ctr[C_ERR]));
             if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
         }
-        const int npairs = ldr(&S.ctr[C_NPAIRS]);
+        const int npairs = T.bcast(ldr(&S.ctr[C_NPAIRS]));
         // connected components of pairs within b_1: min-label propagation
-        for (int s = lane; s < K; s += WS) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
-        __syncwarp();
+        for (int s = T.tid; s < K; s += T.NT) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
+        T.sync();
         for (int round = 0; round <= K; round++) {
             bool changed = false;
-            for (int i = lane; i < npairs; i += WS) {
+            for (int i = T.tid; i < npairs; i += T.NT) {
                 const int sl = S.plist[i];
                 unsigned long long k;
                 int pv;
@@ -1395,17 +1655,17 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
                     changed = true;
                 }
             }
-            __syncwarp();
-            if (!__any_sync(FULL, changed)) break;
+            T.sync();
+            if (!T.any(changed)) break;
         }
-        for (int s = lane; s < K; s += WS) {
+        for (int s = T.tid; s < K; s += T.NT) {
             const int r = S.comp[s];
             atomicAdd(&S.cst0[r], 1);
             const unsigned long long bb = S.sbnd[s];
             if (bb != EMPTY64 && 2LL * (long long)(bb >> 32) <= (long long)g.b1) atomicOr(&S.cst1[r], 1);
         }
-        __syncwarp();
-        for (int i = lane; i < npairs; i += WS) {
+        T.sync();
+        for (int i = T.tid; i < npairs; i += T.NT) {
             const int sl = S.plist[i];
             unsigned long long k;
             int pv;
@@ -1414,10 +1674,10 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
             if (S.comp[a] == S.comp[b]) atomicAdd(&S.cst2[S.comp[a]], 1);
         }
-        __syncwarp();
+        T.sync();
         // ---- level-1 clusters: closed forms for isolated pairs / boundary singletons
         bool need_general = false;
-        for (int s = lane; s < K; s += WS) {
+        for (int s = T.tid; s < K; s += T.NT) {
             const int r = S.comp[s];
             const int size = S.cst0[r];
             const bool ok = (long long)S.cst2[r] == (long long)size * (size - 1) / 2 &&
@@ -1449,13 +1709,13 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
                 atomicOr(&S.cst1[r], 2);
             }
         }
-        __syncwarp();
-        t1 = (int)__reduce_max_sync(FULL, (unsigned)t1);
-        ncl1 = (int)__reduce_add_sync(FULL, (unsigned)ncl1);
-        nres1 = (int)__reduce_add_sync(FULL, (unsigned)nres1);
+        T.sync();
+        t1 = T.maxi(t1);
+        ncl1 = T.add(ncl1);
+        nres1 = T.add(nres1);
         e1 = ncl1 > 0 ? 1 : 0;
         ntot = ncl1;
-        need_general = __any_sync(FULL, need_general);
+        need_general = T.any(need_general);
         gr = need_general ? 0 : K;
     }
     // ---- level-1 clusters without a closed form, one run each (from an empty
@@ -1467,43 +1727,43 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         while (gr < K && (S.comp[gr] != gr || !(S.cst1[gr] & 2))) gr++;
         const bool top = gr >= K;
         if (top) {
-            for (int s = lane; s < K; s += WS) {
+            for (int s = T.tid; s < K; s += T.NT) {
                 if (S.alive[s] || S.stop[s] != s) S.inplay[s] = 1;   // stopped level-1 configuration
                 else make_root(S, s);
             }
             C.ncut = 0;
             C.tcut = t1;
         } else {
-            for (int s = lane; s < K; s += WS)
+            for (int s = T.tid; s < K; s += T.NT)
                 if (S.comp[s] == gr) make_root(S, s);
         }
-        __syncwarp();
+        T.sync();
         C.nm = 0;
         C.tlast = 0;
-        const int st = run_matcher(S, C, lane, nhi);
+        const int st = run_matcher(S, C, T, nhi);
         if (st != RUN_OK) {
             if (st == RUN_CAP) return -1;
             return st == RUN_NOSOL ? QEC_SHOT_NO_SOLUTION
                    : st == RUN_BUDGET ? QEC_SHOT_BUDGET_EXCEEDED : QEC_SHOT_INTERNAL;
         }
         if (top) break;
-        for (int s = lane; s < K; s += WS)
+        for (int s = T.tid; s < K; s += T.NT)
             if (S.comp[s] == gr) S.inplay[s] = 0;
-        __syncwarp();
+        T.sync();
         e1 = max(e1, C.nm); t1 = max(t1, C.tlast); ntot += C.nm; ncl1++; nres1 += S.cst0[gr];
         gr++;
     }
     long long wint = 0;
     unsigned long long ob = 0;
-    trace(S, C, lane, nhi, wint, ob);
+    trace(S, C, T, nhi, wint, ob);
     if constexpr (WIN) {   // sliding window: the committed part
-        if (!ldr(&S.ctr[C_ERR])) ob = commit_trace(S, C, lane, A.carry + (row - A.syn));
+        if (!T.bcast(ldr(&S.ctr[C_ERR]))) ob = commit_trace(S, C, T, A.carry + (row - A.syn));
     }
-    const int err = ldr(&S.ctr[C_ERR]);
+    const int err = T.bcast(ldr(&S.ctr[C_ERR]));
     if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
     w_out = wint / 2;
     o_out = ob;
-    if (dg && lane == 0) {
+    if (dg && T.tid == 0) {
         // parallel event count over level 1 and the top level (Methods,
         // "Numerical evaluation"): the top run's events up to the level-1
         // critical-path time t1 overlap level 1, the rest extend it
@@ -1524,20 +1784,20 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
 // entry and are returned empty: after a successful shot only the slots listed
 // in the band lists and the pair list are reset, after anything else the
 // whole region the attempt could have used.
-template <bool WIN>
-__device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row,
-                              int lane, unsigned scale, unsigned long long deadline, long long &w_out,
+template <bool WIN, int NW>
+__device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g, const unsigned *row, Team<NW> &T,
+                              unsigned scale, unsigned long long deadline, long long &w_out,
                               unsigned long long &o_out, int *dg) {
     Shot C;
     C.hmask = 0;
     C.pmask = 0;
-    const int st = decode_attempt_body<WIN>(A, S, g, row, lane, scale, deadline, w_out, o_out, dg, C);
-    if (C.hmask) release_tables(S, C, lane, st != QEC_SHOT_OK);
+    const int st = decode_attempt_body<WIN, NW>(A, S, g, row, T, scale, deadline, w_out, o_out, dg, C);
+    if (C.hmask) release_tables(S, C, T, st != QEC_SHOT_OK);
     return st;
 }
 
-template <bool WIN>
-__device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, int lane,
+template <bool WIN, int NW>
+__device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, Team<NW> &T,
                             unsigned long long deadline) {
     int gi = A.graph_of_shot ? A.graph_of_shot[shot] : 0;
     if (gi < 0 || gi >= A.num_graphs) gi = 0;
@@ -1549,59 +1809,71 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, i
     unsigned long long o = 0;
     int *dg = A.diag_out ? A.diag_out + shot * QEC_DIAG_FIELDS : nullptr;
     for (unsigned scale = 1; scale <= 64 && status == -1; scale *= 4)
-        status = decode_attempt<WIN>(A, S, g, row, lane, scale, deadline, w, o, dg);
+        status = decode_attempt<WIN, NW>(A, S, g, row, T, scale, deadline, w, o, dg);
     const bool retried = status < 0 && A.pass == 0 && A.single_shot < 0;   // goes to the overflow pass
     if (status < 0) {
         status = QEC_SHOT_CAPACITY;
-        if (retried && lane == 0) {
+        if (retried && T.tid == 0) {
             const unsigned long long idx = atomicAdd(&A.queue[1], 1ull);
             A.overflow[idx] = (int)shot;
         }
         w = 0;
         o = 0;
     }
-    if (dg && status != QEC_SHOT_OK && lane < QEC_DIAG_FIELDS) dg[lane] = 0;
+    if (dg && status != QEC_SHOT_OK && T.tid < QEC_DIAG_FIELDS) dg[T.tid] = 0;
     if constexpr (WIN) {
         // sliding window: nothing is committed by a failed shot
         if (status != QEC_SHOT_OK)
-            for (int i = lane; i < g.words; i += WS) A.carry[off + i] = 0u;
-        if (lane == 0) {
+            for (int i = T.tid; i < g.words; i += T.NT) A.carry[off + i] = 0u;
+        if (T.tid == 0) {
             if (status == QEC_SHOT_OK) A.cobs[shot] ^= o;
             else if (!retried) A.st_out[shot] = status;
         }
-    } else if (lane == 0) {
+    } else if (T.tid == 0) {
         A.w_out[shot] = w;
         A.obs_out[shot] = o;
         A.st_out[shot] = status;
     }
-    __syncwarp();
+    T.sync();
 }
 
-template <bool WIN>
-__global__ void __launch_bounds__(128, QEC_MIN_BLOCKS) batch_kernel(const __grid_constant__ BatchArgs a) {
-    const int lane = threadIdx.x & 31;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// One team per warp (NW = 1, any block size that is a multiple of 32) or one
+// team per block (NW > 1, blocks of exactly 32 NW threads).
+template <bool WIN, int NW>
+__global__ void __launch_bounds__(NW == 1 ? 128 : 32 * NW, NW == 1 ? QEC_MIN_BLOCKS : 1)
+batch_kernel(const __grid_constant__ BatchArgs a) {
+    Team<NW> T;
+    T.sh = nullptr;
+    if constexpr (NW > 1) {
+        __shared__ TeamShared tsh;
+        T.sh = &tsh;
+    }
+    T.lane = threadIdx.x & 31;
+    T.tid = NW == 1 ? T.lane : (int)threadIdx.x;
+    T.warp = NW == 1 ? 0 : (int)(threadIdx.x >> 5);
+    T.ph = 0;
+    const long long wid = NW == 1 ? (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) : (long long)blockIdx.x;
     Slab S;
     carve(a.slabs + wid * a.slab_bytes, a.caps, S);
     unsigned long long deadline = 0;
     if (a.watchdog_ns > 0) {
-        unsigned long long t0 = lane == 0 ? now_ns() : 0;
-        deadline = __shfl_sync(FULL, t0, 0) + (unsigned long long)a.watchdog_ns;
+        unsigned long long t0 = T.tid == 0 ? now_ns() : 0;
+        deadline = T.bcast64(t0) + (unsigned long long)a.watchdog_ns;
     }
     if (a.single_shot >= 0) {
-        if (wid == 0) decode_shot<WIN>(a, S, a.single_shot, lane, deadline);
+        if (wid == 0) decode_shot<WIN, NW>(a, S, a.single_shot, T, deadline);
         return;
     }
     unsigned long long *counter = a.queue + (a.pass == 0 ? 0 : 2);
     const long long limit = a.pass == 0 ? a.num_shots : (long long)min(a.queue[1], (unsigned long long)a.num_shots);
     for (long long it = 0; it < a.num_shots + 1; it++) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(counter, 1ull);
-        item = __shfl_sync(FULL, item, 0);
+        if (T.tid == 0) item = atomicAdd(counter, 1ull);
+        item = T.bcast64(item);
         if ((long long)item >= limit) break;
         const long long shot = a.pass == 0 ? (a.order ? (long long)a.order[item] : (long long)item)
                                            : (long long)a.overflow[item];
-        decode_shot<WIN>(a, S, shot, lane, deadline);
+        decode_shot<WIN, NW>(a, S, shot, T, deadline);
     }
 }
 
@@ -1678,21 +1950,37 @@ SlabCaps caps_for_kcap(int kcap, int table_factor) {
     return c;
 }
 
-cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s) {
-    if (a.carry) batch_kernel<true><<<grid, block, 0, s>>>(a);
-    else batch_kernel<false><<<grid, block, 0, s>>>(a);
+cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s, int team) {
+    if (a.carry) {
+        batch_kernel<true, 1><<<grid, block, 0, s>>>(a);
+    } else if (team == TEAM_BIG) {
+        batch_kernel<false, TEAM_BIG><<<grid, 32 * TEAM_BIG, 0, s>>>(a);
+    } else if (team == TEAM_MID) {
+        batch_kernel<false, TEAM_MID><<<grid, 32 * TEAM_MID, 0, s>>>(a);
+    } else {
+        batch_kernel<false, 1><<<grid, block, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 int max_block_threads() {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, batch_kernel<false>) != cudaSuccess) return 32;
+    if (cudaFuncGetAttributes(&fa, batch_kernel<false, 1>) != cudaSuccess) return 32;
     return fa.maxThreadsPerBlock > 0 ? fa.maxThreadsPerBlock : 32;
 }
 
 int occupancy_blocks(int block_threads) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<false>, block_threads, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<false, 1>, block_threads, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
+}
+
+int team_occupancy_blocks(int team) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (team == TEAM_BIG) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<false, TEAM_BIG>, 32 * TEAM_BIG, 0);
+    else if (team == TEAM_MID) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<false, TEAM_MID>, 32 * TEAM_MID, 0);
+    if (e != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
 }
 

@@ -82,7 +82,15 @@ long long slab_bytes_for(const SlabCaps &c);
 // Slab capacities for `kcap` detection events; hash tables and entry lists get
 // table_factor times the default room per event.
 SlabCaps caps_for_kcap(int kcap, int table_factor = 1);
-cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s);
+// Team sizes compiled besides one warp per shot: a whole block of TEAM_MID or
+// TEAM_BIG warps decodes one shot (large windows, single-window latency).
+constexpr int TEAM_MID = 4;
+constexpr int TEAM_BIG = 16;
+// Launch the batch kernel: team 1 = one warp per shot (grid x block threads),
+// TEAM_MID / TEAM_BIG = one block of that many warps per shot (grid blocks).
+cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s, int team = 1);
+// Resident blocks per SM of the multi-warp batch kernel of team size `team`.
+int team_occupancy_blocks(int team);
 cudaError_t launch_reset_queue(unsigned long long *queue, cudaStream_t s);
 // Window syndromes from stream syndromes: bit i of window row r is bit
 // (bit_begin + i) of stream row r for i < nbits, XOR bit (carry_begin + i) of

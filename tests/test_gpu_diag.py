@@ -179,3 +179,27 @@ def test_custom_schedule_matches_oracle(qd, sname, spec):
         # event count is compared on every shot
         assert multi == 0, (sname, multi)
         assert g.info.upper_single_cluster == 1
+
+
+def test_distance_bound_and_single_upper_cluster(qd):
+    """qec_graph_info.distance_bound is an upper bound of the largest distance
+    between connected detectors, at most twice it (scipy Dijkstra from every
+    detector); upper_single_cluster holds for the rotated codes and not for a
+    graph of two components."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import dijkstra
+    from synth import rotated_surface_code_circuit
+    for pg in (rotated_surface_code(5, 5, 0.005), rotated_surface_code(9, 9, 0.003),
+               rotated_surface_code(7, 7, p_range=(0.001, 0.02), p_seed=4), rotated_surface_code_circuit(5, 5, 0.003)):
+        g = qd.Graph.from_phys(pg)
+        u, v, w, _ = g.merged_edges()
+        m = v >= 0
+        n = pg.num_detectors
+        A = coo_matrix((w[m].astype(float), (u[m], v[m])), shape=(n, n)).tocsr()
+        D = dijkstra(A, directed=False)
+        diam = D[np.isfinite(D)].max()
+        assert diam <= g.info.distance_bound <= 2 * diam
+        assert g.info.components == 1 and g.info.upper_single_cluster == 1
+    # two disjoint paths: two components
+    g = qd.Graph(8, [0, 1, 2, 4, 5, 6, 0, 4], [1, 2, 3, 5, 6, 7, -1, -1], [3] * 8, [0] * 8)
+    assert g.info.components == 2 and g.info.upper_single_cluster == 0
