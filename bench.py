@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving run length (0 = skip); 5 s = 10^6 windows at 200k/s")
     ap.add_argument("--serve-rate", type=float, default=200000.0, help="Poisson arrival rate, windows/s")
     ap.add_argument("--serve-oracle", type=int, default=3000, help="served windows checked against the oracle")
+    ap.add_argument("--serve-curve", type=int, default=1, help="also serve at 50k, 100k and 400k windows/s")
+    ap.add_argument("--extra-configs", type=int, default=1,
+                    help="add the d=5 / d=11 configurations and the d=25..51 per-round scaling to the line")
+    ap.add_argument("--serve-curve-seconds", type=float, default=2.0)
     ap.add_argument("--scaling", action="store_true",
                     help="scaling study: d in {25,31,41,51} x p in {.001,.003,.005}, us per round vs d")
     ap.add_argument("--scaling-shots", type=int, default=10000)
@@ -301,17 +305,24 @@ def cpu_oracle_one_core(graphs, gid, offs, syn, seconds):
     return done / t_used, done
 
 
-def serving_run(q, args, dev):
-    """Poisson arrivals into a qec_stream; latency = result time - scheduled arrival."""
-    import torch
+def serving_data(q, args, n):
+    """n windows of the serving workload: d uniform in {9, 13, 17, 21, 25}, d
+    rounds, p, shuffled; graphs resident on the device."""
     sds = [9, 13, 17, 21, 25]
-    N = int(args.serve_rate * args.serve_seconds)
-    per_d = (N + len(sds) - 1) // len(sds)
+    per_d = (n + len(sds) - 1) // len(sds)
     graphs, gid, offs, syn = mixed_batch(sds, per_d, args.p, seed=args.seed + 77)
-    gid, offs = gid[:N], offs[:N]
-    gg = [q.Graph.from_phys(g) for g in graphs]
+    return sds, graphs, [q.Graph.from_phys(g) for g in graphs], gid[:n], offs[:n], syn
+
+
+def serving_run(q, args, dev, data, rate, seconds, oracle_n=0):
+    """Poisson arrivals at `rate` windows/s for `seconds` into a qec_stream;
+    latency = result time - scheduled arrival."""
+    import torch
+    sds, graphs, gg, gid_all, offs_all, syn = data
+    N = min(int(rate * seconds), gid_all.shape[0])
+    gid, offs = gid_all[:N], offs_all[:N]
     rng = np.random.default_rng(args.seed + 78)
-    arr = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=N))
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=N))
     st = q.Stream(device_budget_bytes=6 << 30, max_inflight=65536)
     try:
         warm = min(2000, N)
@@ -326,7 +337,7 @@ def serving_run(q, args, dev):
         got_w = np.zeros(N, np.int64); got_o = np.zeros(N, np.uint64); got_s = np.full(N, -1, np.int32)
         t_done = np.zeros(N, np.int64)
         i, n_done = 0, 0
-        deadline = time.monotonic() + 30 + 4 * args.serve_seconds
+        deadline = time.monotonic() + 30 + 4 * seconds
         while n_done < N and time.monotonic() < deadline:
             now = time.monotonic_ns()
             j = int(np.searchsorted(sched, now, side="right"))
@@ -351,10 +362,10 @@ def serving_run(q, args, dev):
     mism = int(np.count_nonzero(ok & ((bw != got_w) | (bo != got_o) | (bs != got_s))))
     # served results against the oracle, on a uniform sample of the windows
     oracle_check = None
-    if args.serve_oracle > 0 and ok.any():
+    if oracle_n > 0 and ok.any():
         sys.path.insert(0, os.path.join(ROOT, "tests"))
         from oracle_pool import OraclePool
-        pick = np.random.default_rng(args.seed + 79).choice(np.nonzero(ok)[0], size=min(args.serve_oracle, int(ok.sum())),
+        pick = np.random.default_rng(args.seed + 79).choice(np.nonzero(ok)[0], size=min(oracle_n, int(ok.sum())),
                                                             replace=False)
         pool = OraclePool(graphs, os.cpu_count() or 1)
         rows = [syn[offs[k]:offs[k] + graphs[gid[k]].words] for k in pick]
@@ -363,12 +374,32 @@ def serving_run(q, args, dev):
         oracle_check = {"checked": int(pick.size), "mismatches": int(np.count_nonzero(
             (rw != got_w[pick]) | (ro != got_o[pick]) | (rs != got_s[pick]))),
             "sample": "uniformly drawn served windows, compared on weight, observable and status"}
-    return {"windows": N, "completed": int(ok.sum()), "offered_rate": args.serve_rate,
+    return {"windows": N, "completed": int(ok.sum()), "offered_rate": rate,
             "sustained": float(ok.sum() / span), "unit": "windows/s",
             "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
             "p999_us": float(np.percentile(lat_us, 99.9)), "max_us": float(lat_us.max()),
             "distances": sds, "p": args.p, "mismatch_vs_batch": mism, "oracle": oracle_check,
+            "team_warps": q.get_tuning()["team_warps"] or "auto",
             "latency": "result available on the host minus the scheduled Poisson arrival"}
+
+
+def serving_all(q, args, dev):
+    """The serving record at the offered rate of the workload (with the oracle
+    check) and the latency at other offered rates (latency versus load)."""
+    rates = sorted(set([args.serve_rate] + [r for r in (50000.0, 100000.0, 400000.0) if args.serve_curve]))
+    n = max(int(args.serve_rate * args.serve_seconds), max(int(r * args.serve_curve_seconds) for r in rates))
+    data = serving_data(q, args, n)
+    main = serving_run(q, args, dev, data, args.serve_rate, args.serve_seconds, args.serve_oracle)
+    curve = []
+    for r in rates:
+        if r == args.serve_rate:
+            rec = main
+        else:
+            rec = serving_run(q, args, dev, data, r, args.serve_curve_seconds)
+        curve.append({k: rec[k] for k in ("offered_rate", "sustained", "windows", "p50_us", "p99_us", "p999_us",
+                                          "mismatch_vs_batch")})
+    main["latency_vs_load"] = curve
+    return main
 
 
 def scaling_study(q, args, dev):
@@ -396,7 +427,8 @@ def scaling_study(q, args, dev):
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
             st = out[2].cpu().numpy()
-            # single-window latency: one window per launch
+            # single-window latency: one window per launch, one warp (the plain
+            # path) and a 16-warp team (one window alone in a batch)
             nl = min(16, S)
             po = (torch.empty(nl, dtype=torch.int64, device=dev), torch.empty(nl, dtype=torch.int64, device=dev),
                   torch.empty(nl, dtype=torch.int32, device=dev))
@@ -406,10 +438,24 @@ def scaling_study(q, args, dev):
             q.decode_plain(g, t, num_shots=nl, out=po)
             b.record()
             torch.cuda.synchronize()
-            lat_ms = a.elapsed_time(b) / nl
+            warp_lat_ms = a.elapsed_time(b) / nl
+            q.set_tuning(team_warps=16)
+            tl = []
+            for k in range(-1, nl):
+                kk = max(k, 0)
+                r1 = (po[0][kk:kk + 1], po[1][kk:kk + 1], po[2][kk:kk + 1])
+                a.record()
+                q.decode_batch([g], t[kk * pg.words:(kk + 1) * pg.words], num_shots=1, out=r1)
+                b.record()
+                torch.cuda.synchronize()
+                if k >= 0:
+                    tl.append(a.elapsed_time(b))
+            q.set_tuning(team_warps=-1)
+            lat_ms = float(np.mean(tl))
             row = {"d": d, "rounds": d, "p": p, "windows": S, "mean_events": float(pc.mean()), "max_events": kmax,
                    "batch_ms": ms, "windows_per_s": S / (ms / 1e3), "us_per_round_throughput": ms * 1e3 / S / d,
                    "window_latency_us": lat_ms * 1e3, "us_per_round_latency": lat_ms * 1e3 / d,
+                   "one_warp_latency_us": warp_lat_ms * 1e3, "team_speedup": warp_lat_ms / lat_ms,
                    "nonzero_status": int(np.count_nonzero(st))}
             if args.scaling_save:
                 os.makedirs(args.scaling_save, exist_ok=True)
@@ -656,6 +702,116 @@ def event_study(q, args, dev):
     return rows
 
 
+def configs_line(q, args, dev):
+    """The small and non-uniform configurations in the bench line: d = 5 (p =
+    0.005, 10,000 shots from seed 0) and d = 11 (per-edge p ~ U[0.002, 0.006],
+    100,000 shots), batched (one persistent launch) and plain (one launch per
+    shot), in shots/s and us per round; the plain and batched outputs agree."""
+    import torch
+    out = {}
+    cases = [("d5_p0.005", rotated_surface_code(5, 5, 0.005), 10000, 0, 10000),
+             ("d11_U[0.002,0.006]", rotated_surface_code(11, 11, p_range=(0.002, 0.006), p_seed=1), 100000, 1, 4000)]
+    for name, pg, S, seed, n_plain in cases:
+        syn, _ = sample_shots(pg, S, seed)
+        g = q.Graph.from_phys(pg)
+        t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
+        res = (torch.empty(S, dtype=torch.int64, device=dev), torch.empty(S, dtype=torch.int64, device=dev),
+               torch.empty(S, dtype=torch.int32, device=dev))
+        for _ in range(3):
+            q.decode_batch([g], t, num_shots=S, out=res)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record()
+        for _ in range(reps):
+            q.decode_batch([g], t, num_shots=S, out=res)
+        b.record()
+        torch.cuda.synchronize()
+        batch_rate = reps * S / (a.elapsed_time(b) / 1e3)
+        po = (torch.empty(n_plain, dtype=torch.int64, device=dev), torch.empty(n_plain, dtype=torch.int64, device=dev),
+              torch.empty(n_plain, dtype=torch.int32, device=dev))
+        q.decode_plain(g, t, num_shots=min(200, n_plain), out=po)
+        torch.cuda.synchronize()
+        a.record()
+        q.decode_plain(g, t, num_shots=n_plain, out=po)
+        b.record()
+        torch.cuda.synchronize()
+        plain_rate = n_plain / (a.elapsed_time(b) / 1e3)
+        out[name] = {"shots": S, "rounds": pg.rounds, "batched_shots_per_s": batch_rate,
+                     "batched_us_per_round": 1e6 / batch_rate / pg.rounds, "plain_shots_per_s": plain_rate,
+                     "plain_shots": n_plain, "plain_us_per_round": 1e6 / plain_rate / pg.rounds,
+                     "batched_over_plain": batch_rate / plain_rate,
+                     "plain_equals_batched": bool(torch.equal(po[1], res[1][:n_plain]) and
+                                                  torch.equal(po[0], res[0][:n_plain])),
+                     "nonzero_status": int(torch.count_nonzero(res[2]).item())}
+        del t, res, po
+    return out
+
+
+def scaling_line(q, args, dev):
+    """Per-round decode time versus d at p = 0.003 for single large windows (d
+    rounds): batched throughput over many windows (one warp per window) and the
+    latency of one window decoded alone (a 16-warp team per window, and one
+    warp for comparison); the single windows are checked against the oracle."""
+    import torch
+    out = {}
+    checks = []
+    for d, n in ((25, 4000), (31, 3000), (41, 1500), (51, 800)):
+        pg = rotated_surface_code(d, d, 0.003)
+        syn, _ = sample_shots(pg, n, args.seed + 500 + d)
+        K = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)
+        g = q.Graph.from_phys(pg)
+        t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
+        q.set_tuning(kcap=max(64, int(K.max() * 1.1) + 8), team_warps=1)
+        res = (torch.empty(n, dtype=torch.int64, device=dev), torch.empty(n, dtype=torch.int64, device=dev),
+               torch.empty(n, dtype=torch.int32, device=dev))
+        q.decode_batch([g], t, num_shots=n, out=res)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        q.decode_batch([g], t, num_shots=n, out=res)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        lat = {}
+        one = []
+        for team in (16, 1):
+            q.set_tuning(team_warps=team)
+            times = []
+            for s in range(-1, 6):
+                k = max(s, 0)
+                r1 = (res[0][k:k + 1].clone(), res[1][k:k + 1].clone(), res[2][k:k + 1].clone())
+                a.record()
+                q.decode_batch([g], t[k * pg.words:(k + 1) * pg.words], num_shots=1, out=r1)
+                b.record()
+                torch.cuda.synchronize()
+                if s >= 0:
+                    times.append(a.elapsed_time(b))
+                    if team == 16:
+                        one.append((int(r1[1].item()), int(r1[0].item()) & ((1 << 64) - 1), int(r1[2].item())))
+            lat[team] = float(np.mean(times))
+        out["d%d" % d] = {"d": d, "rounds": d, "p": 0.003, "windows": n, "mean_events": float(K.mean()),
+                          "batched_windows_per_s": n / (ms / 1e3), "batched_us_per_round": ms * 1e3 / n / d,
+                          "latency_us": lat[16] * 1e3, "latency_us_per_round": lat[16] * 1e3 / d,
+                          "latency_team_warps": 16, "one_warp_latency_us": lat[1] * 1e3,
+                          "team_speedup": lat[1] / lat[16],
+                          "nonzero_status": int(torch.count_nonzero(res[2]).item())}
+        checks.append((pg, syn[:2], one[:2]))
+        del t, res
+    q.set_tuning(kcap=-1, team_warps=-1)
+    # the first two single windows of every distance against the oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle_pool import oracle_decode
+    phys = [c[0] for c in checks]
+    gid = np.repeat(np.arange(len(checks), dtype=np.int32), 2)
+    rows = [r for c in checks for r in c[1]]
+    rw, ro, rs = oracle_decode(phys, gid, rows, chunk=1, workers=min(len(rows), os.cpu_count() or 1))
+    got = [x for c in checks for x in c[2]]
+    bad = sum(1 for i, (w, o, st) in enumerate(got) if (w, o, st) != (int(rw[i]), int(ro[i]), int(rs[i])))
+    out["parity"] = {"checked": len(got), "mismatches": bad, "against": "oracle, the single windows"}
+    return out
+
+
 def reference_arm(args, ws, rank):
     if ws > 1 and rank != 0:
         return
@@ -701,6 +857,7 @@ def main():
         args.plain_shots = min(args.plain_shots, 200)
         args.no_cpu_baseline = True
         args.serve_seconds = 0
+        args.extra_configs = 0
     if args.impl == "reference":
         return reference_arm(args, ws, rank)
     import torch
@@ -853,7 +1010,12 @@ def main():
 
     serving = None
     if args.serve_seconds > 0 and rank == 0:
-        serving = serving_run(q, args, dev)
+        serving = serving_all(q, args, dev)
+
+    configs = scaling = None
+    if rank == 0 and ws == 1 and args.extra_configs:
+        configs = configs_line(q, args, dev)
+        scaling = scaling_line(q, args, dev)
 
     cpu = None
     parity = None
@@ -895,6 +1057,8 @@ def main():
             "serving": serving,
             "cpu_baseline": cpu,
             "parity": parity,
+            "configs": configs,
+            "scaling_p003": scaling,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -356,7 +356,10 @@ int qec_decode_batch_static(const qec_graph *const *graphs, int32_t num_graphs,
  * overlap on the device (one CUDA stream and scratch workspace per slot).
  * Graphs stay resident; results are read back into pinned memory and handed
  * out by qec_stream_poll.  Each result is the same as decoding the window
- * alone with qec_decode_batch. */
+ * alone with qec_decode_batch.  Each window of a micro-batch is decoded by a
+ * team of qec_tuning.team_warps warps; automatic: a thread block of 16 warps
+ * per window while the micro-batch has no more windows than the GPU holds such
+ * blocks at once, else one warp per window. */
 #define QEC_STREAM_MAX_WORDS 2304          /* largest window: 73,728 detectors */
 #define QEC_STREAM_MAX_GRAPHS QEC_MAX_GRAPHS_PER_BATCH
 

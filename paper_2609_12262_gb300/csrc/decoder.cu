@@ -63,6 +63,9 @@
 #include "qec_internal.h"
 
 #define WS 32   // lanes per warp
+#ifndef QEC_HT_FACTOR
+#define QEC_HT_FACTOR 64   // explored-table slots per detection event (rounded up to a power of two)
+#endif
 #ifndef QEC_MIN_BLOCKS
 #define QEC_MIN_BLOCKS 6   // 128-thread blocks per SM the register budget must allow
 #endif
@@ -172,20 +175,36 @@ __device__ __forceinline__ unsigned long long warp_xor64(unsigned long long v) {
 
 // Shared scratch of a multi-warp team: one slot per warp for reductions, in
 // two alternating buffers (every team operation ends with one barrier, so a
-// buffer is reused only after every thread has read it).
+// buffer is reused only after every thread has read it).  Functions kept out
+// of line take their Team by value and end with a barrier after their last
+// team operation, so the caller may go on with its own buffer parity.
 struct TeamShared {
     unsigned long long u64[2][32];
     int i32[2][32][2];
 };
 
+// Per-thread identity of a team member: a one-warp team needs only the lane
+// (its thread index is the lane, its warp 0, and it has no shared scratch).
 template <int NW>
-struct Team {
-    static constexpr int NT = WS * NW;
-    int tid;    // thread in the team, 0 .. NT - 1
-    int lane;   // lane in its warp
-    int warp;   // warp in the team, 0 .. NW - 1
-    int ph;     // buffer parity of the next team operation
+struct TeamId {
+    int tid_, lane, warp_, ph;
     TeamShared *sh;
+    __device__ __forceinline__ int tid() const { return tid_; }
+    __device__ __forceinline__ int warp() const { return warp_; }
+};
+template <>
+struct TeamId<1> {
+    int lane;
+    __device__ __forceinline__ int tid() const { return lane; }
+    __device__ __forceinline__ int warp() const { return 0; }
+};
+
+template <int NW>
+struct Team : TeamId<NW> {
+    static constexpr int NT = WS * NW;
+    using TeamId<NW>::lane;
+    using TeamId<NW>::tid;
+    using TeamId<NW>::warp;
 
     __device__ __forceinline__ void sync() const {
         if constexpr (NW == 1) __syncwarp(); else __syncthreads();
@@ -195,10 +214,10 @@ struct Team {
         if constexpr (NW == 1) {
             return __shfl_sync(FULL, v, 0);
         } else {
-            if (tid == 0) sh->i32[ph][0][0] = v;
+            if (tid() == 0) this->sh->i32[this->ph][0][0] = v;
             __syncthreads();
-            v = sh->i32[ph][0][0];
-            ph ^= 1;
+            v = this->sh->i32[this->ph][0][0];
+            this->ph ^= 1;
             return v;
         }
     }
@@ -206,10 +225,10 @@ struct Team {
         if constexpr (NW == 1) {
             return __shfl_sync(FULL, v, 0);
         } else {
-            if (tid == 0) sh->u64[ph][0] = v;
+            if (tid() == 0) this->sh->u64[this->ph][0] = v;
             __syncthreads();
-            v = sh->u64[ph][0];
-            ph ^= 1;
+            v = this->sh->u64[this->ph][0];
+            this->ph ^= 1;
             return v;
         }
     }
@@ -218,11 +237,11 @@ struct Team {
         if constexpr (NW == 1) {
             return v;
         } else {
-            if (lane == 0) sh->u64[ph][warp] = v;
+            if (lane == 0) this->sh->u64[this->ph][warp()] = v;
             __syncthreads();
-            unsigned long long r = sh->u64[ph][0];
-            for (int w = 1; w < NW; w++) { const unsigned long long x = sh->u64[ph][w]; r = x < r ? x : r; }
-            ph ^= 1;
+            unsigned long long r = this->sh->u64[this->ph][0];
+            for (int w = 1; w < NW; w++) { const unsigned long long x = this->sh->u64[this->ph][w]; r = x < r ? x : r; }
+            this->ph ^= 1;
             return r;
         }
     }
@@ -231,11 +250,11 @@ struct Team {
         if constexpr (NW == 1) {
             return v;
         } else {
-            if (lane == 0) sh->u64[ph][warp] = (unsigned long long)v;
+            if (lane == 0) this->sh->u64[this->ph][warp()] = (unsigned long long)v;
             __syncthreads();
             long long r = 0;
-            for (int w = 0; w < NW; w++) r += (long long)sh->u64[ph][w];
-            ph ^= 1;
+            for (int w = 0; w < NW; w++) r += (long long)this->sh->u64[this->ph][w];
+            this->ph ^= 1;
             return r;
         }
     }
@@ -244,11 +263,11 @@ struct Team {
         if constexpr (NW == 1) {
             return v;
         } else {
-            if (lane == 0) sh->u64[ph][warp] = v;
+            if (lane == 0) this->sh->u64[this->ph][warp()] = v;
             __syncthreads();
             unsigned long long r = 0;
-            for (int w = 0; w < NW; w++) r ^= sh->u64[ph][w];
-            ph ^= 1;
+            for (int w = 0; w < NW; w++) r ^= this->sh->u64[this->ph][w];
+            this->ph ^= 1;
             return r;
         }
     }
@@ -261,14 +280,14 @@ struct Team {
         if constexpr (NW == 1) {
             return v;
         } else {
-            if (lane == 0) sh->i32[ph][warp][0] = v;
+            if (lane == 0) this->sh->i32[this->ph][warp()][0] = v;
             __syncthreads();
-            int r = sh->i32[ph][0][0];
+            int r = this->sh->i32[this->ph][0][0];
             for (int w = 1; w < NW; w++) {
-                const int x = sh->i32[ph][w][0];
+                const int x = this->sh->i32[this->ph][w][0];
                 r = OP == 0 ? r + x : (OP == 1 ? (x > r ? x : r) : (r | x));
             }
-            ph ^= 1;
+            this->ph ^= 1;
             return r;
         }
     }
@@ -283,22 +302,22 @@ struct Team {
         m = __reduce_min_sync(FULL, m);
         if constexpr (NW > 1) {
             if (lane == 0) {
-                sh->u64[ph][warp] = key;
-                sh->i32[ph][warp][0] = flags;
-                sh->i32[ph][warp][1] = (int)m;
+                this->sh->u64[this->ph][warp()] = key;
+                this->sh->i32[this->ph][warp()][0] = flags;
+                this->sh->i32[this->ph][warp()][1] = (int)m;
             }
             __syncthreads();
-            key = sh->u64[ph][0];
-            flags = sh->i32[ph][0][0];
-            m = (unsigned)sh->i32[ph][0][1];
+            key = this->sh->u64[this->ph][0];
+            flags = this->sh->i32[this->ph][0][0];
+            m = (unsigned)this->sh->i32[this->ph][0][1];
             for (int w = 1; w < NW; w++) {
-                const unsigned long long x = sh->u64[ph][w];
+                const unsigned long long x = this->sh->u64[this->ph][w];
                 key = x < key ? x : key;
-                flags |= sh->i32[ph][w][0];
-                const unsigned y = (unsigned)sh->i32[ph][w][1];
+                flags |= this->sh->i32[this->ph][w][0];
+                const unsigned y = (unsigned)this->sh->i32[this->ph][w][1];
                 m = y < m ? y : m;
             }
-            ph ^= 1;
+            this->ph ^= 1;
         }
     }
     // Exclusive prefix sum of v over the team's threads in tid order; `total`
@@ -315,15 +334,15 @@ struct Team {
             total = wtot;
             return incl - v;
         } else {
-            if (lane == 0) sh->i32[ph][warp][0] = wtot;
+            if (lane == 0) this->sh->i32[this->ph][warp()][0] = wtot;
             __syncthreads();
             int off = 0, tot = 0;
             for (int w = 0; w < NW; w++) {
-                const int x = sh->i32[ph][w][0];
-                if (w < warp) off += x;
+                const int x = this->sh->i32[this->ph][w][0];
+                if (w < warp()) off += x;
                 tot += x;
             }
-            ph ^= 1;
+            this->ph ^= 1;
             total = tot;
             return off + incl - v;
         }
@@ -553,16 +572,16 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
     if (nx <= 0) return;
     const int lane = T.lane;
     T.sync();
-    if (T.tid == 0) {
+    if (T.tid() == 0) {
         S.ctr[C_TL] = 0; S.ctr[C_WL] = 0;
         if constexpr (NW > 1) { S.ctr[C_R0] = 0; S.ctr[C_R0 + 1] = 0; }
     }
-    for (int i = T.tid; i < nx; i += T.NT) { S.xcnt[i] = 0; S.xidx[S.xsrc[i]] = i; }
+    for (int i = T.tid(); i < nx; i += T.NT) { S.xcnt[i] = 0; S.xidx[S.xsrc[i]] = i; }
     T.sync();
     unsigned *F = reinterpret_cast<unsigned *>(S.wl0), *Wn = reinterpret_cast<unsigned *>(S.wl1);
     // initial frontier: the previous band of every listed source; a source
     // never explored so far starts from its own vertex at distance 0
-    for (int i = T.tid; i < nx; i += T.NT) {
+    for (int i = T.tid(); i < nx; i += T.NT) {
         const int s = S.xsrc[i];
         if (S.sR[s] < 0) {
             unsigned hs;
@@ -592,17 +611,17 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
     int ntl = ldr(&S.ctr[C_TL]);
     const unsigned lt = (1u << lane) - 1u;
     for (int iter = 0;; iter++) {
-        if (iter >= 4096) { if (T.tid == 0) set_err(S, ERR_INTERNAL); break; }
+        if (iter >= 4096) { if (T.tid() == 0) set_err(S, ERR_INTERNAL); break; }
         int nwl = 0;
         int *const wctr = &S.ctr[C_R0 + iter % 3];
         if constexpr (NW > 1) {
-            if (T.tid == 0) S.ctr[C_R0 + (iter + 1) % 3] = 0;
+            if (T.tid() == 0) S.ctr[C_R0 + (iter + 1) % 3] = 0;
         }
         // one lane per (work item, adjacency slot): items are taken 32 at a
         // time per warp, their slots numbered by a warp prefix sum of the
         // degrees, and slot t goes to lane t mod 32 (its item found by binary
         // search)
-        for (int base = T.warp * WS; base < nf; base += T.NT) {
+        for (int base = T.warp() * WS; base < nf; base += T.NT) {
             const int i = base + lane;
             unsigned long long key = 0;
             int dx = 0, Rn = -1, r0 = 0, deg = 0, xi = 0;
@@ -687,18 +706,35 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
     const int e0 = T.bcast(ldr(&S.ctr[C_ECOUNT]));
     // explored-entry table at most half full, list room left
     if (e0 + nt > C.ec || (unsigned)(e0 + nt) * 2u > C.hmask) {
-        if (T.tid == 0) set_err(S, ERR_CAP);
+        if (T.tid() == 0) set_err(S, ERR_CAP);
         T.sync();
         return;
     }
     // bands made contiguous per source (counting sort of the new entries)
-    for (int i = T.tid; i < nt; i += T.NT) atomicAdd(&S.xcnt[(int)(unsigned)(S.tl[i] & 0xffffffffu)], 1);
+    for (int i = T.tid(); i < nt; i += T.NT) atomicAdd(&S.xcnt[(int)(unsigned)(S.tl[i] & 0xffffffffu)], 1);
     T.sync();
-    {
+    if constexpr (NW == 1) {
+        // band starts in list order, by lane 0 (a warp extends only a few
+        // sources at a time; measured faster than a warp-wide scan)
+        if (lane == 0) {
+            int acc = e0;
+            for (int i = 0; i < nx; i++) {
+                const int s = S.xsrc[i];
+                const int c = S.xcnt[i];
+                S.xcur[i] = acc;
+                S.sbeg[s] = acc;
+                S.scnt[s] = c;
+                S.sR[s] = S.xR[i];
+                if (c == 0) S.sexh[s] = 1;
+                acc += c;
+            }
+            S.ctr[C_ECOUNT] = acc;
+        }
+    } else {
         // band starts: exclusive prefix sum of the counts in list order, each
         // thread one contiguous chunk of the list
         const int per = (nx + T.NT - 1) / T.NT;
-        const int i0 = min(nx, T.tid * per), i1 = min(nx, i0 + per);
+        const int i0 = min(nx, T.tid() * per), i1 = min(nx, i0 + per);
         int loc = 0;
         for (int i = i0; i < i1; i++) loc += S.xcnt[i];
         int total = 0;
@@ -713,13 +749,13 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
             if (c == 0) S.sexh[s] = 1;
             acc += c;
         }
-        if (T.tid == 0) {
+        if (T.tid() == 0) {
             S.ctr[C_ECOUNT] = e0 + total;
             S.ctr[C_NEXT] = 0;
         }
     }
     T.sync();
-    for (int i = T.tid; i < nt; i += T.NT) {
+    for (int i = T.tid(); i < nt; i += T.NT) {
         const unsigned long long it = S.tl[i];
         const int pos = atomicAdd(&S.xcur[(int)(unsigned)(it & 0xffffffffu)], 1);
         S.ent[pos] = (int)(it >> 32);
@@ -791,7 +827,7 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
 // Grow one source's ball by one band.  Every thread of the team calls.
 template <int NW>
 __device__ void extend_one(const Slab &S, const Shot &C, int s, Team<NW> &T) {
-    if (T.tid == 0) { S.xsrc[0] = s; S.xR[0] = max(S.sR[s], 0) + C.band; }
+    if (T.tid() == 0) { S.xsrc[0] = s; S.xR[0] = max(S.sR[s], 0) + C.band; }
     T.sync();
     extend_many(S, C, 1, T);
 }
@@ -820,9 +856,9 @@ __device__ void flip_to_root(const Slab &S, int A) {
 
 // Events (b), (f), (g).  B < 0: boundary.  Every thread of the team calls.
 template <int NW>
-__device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, int B, int b, Team<NW> &T, int nhi) {
+__device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, int B, int b, Team<NW> T, int nhi) {
     int rA = 0, rB = -3;
-    if (T.tid == 0) {
+    if (T.tid() == 0) {
         rA = S.nroot[A];
         const bool bout = B >= 0 && S.label[B] == 1;
         rB = bout ? S.nroot[B] : -3;
@@ -838,7 +874,7 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
     rA = T.bcast(rA);
     rB = T.bcast(rB);
     T.sync();
-    for (int v = T.tid; v < nhi; v += T.NT) {
+    for (int v = T.tid(); v < nhi; v += T.NT) {
         if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0 && (S.nroot[v] == rA || S.nroot[v] == rB)) {
             S.label[v] = 0; S.tpar[v] = -1; S.nroot[v] = -1;
         }
@@ -855,9 +891,9 @@ __device__ void ev_grow(const Slab &S, int A, int a, int B, int b) {
 
 // Event (c): outer A, B in one tree form a blossom.  Every thread of the team calls.
 template <int NW>
-__device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, int B, int b, Team<NW> &T, int &nhi) {
+__device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, int B, int b, Team<NW> T, int &nhi) {
     int N = -1, L = -1, Lroot = 0;
-    if (T.tid == 0) {
+    if (T.tid() == 0) {
         int na = 0, nb = 0;
         for (int v = A; v >= 0 && na < 2 * C.nc; v = S.tpar[v]) S.tmpa[na++] = v;
         for (int v = B; v >= 0 && nb < 2 * C.nc; v = S.tpar[v]) S.tmpb[nb++] = v;
@@ -900,7 +936,7 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
     T.sync();
     if (N < 0) return;
     nhi = max(nhi, N + 1);
-    for (int v = T.tid; v < nhi; v += T.NT) {
+    for (int v = T.tid(); v < nhi; v += T.NT) {
         if (!S.alive[v] || S.bpar[v] >= 0 || v == N) continue;
         const int tp = S.tpar[v];
         if (tp >= 0 && S.bpar[tp] == N) S.tpar[v] = N;
@@ -908,7 +944,7 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
         if (mt >= 0 && S.bpar[mt] == N) S.mate[v] = N;
         if (Lroot && S.nroot[v] == L) S.nroot[v] = N;
     }
-    for (int s = T.tid; s < C.K; s += T.NT) {
+    for (int s = T.tid(); s < C.K; s += T.NT) {
         const int tp = S.stop[s];
         if (tp != N && S.bpar[tp] == N) S.stop[s] = N;
     }
@@ -917,14 +953,14 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
 
 // Event (d): inner blossom B with zero dual shatters.  Every thread of the team calls.
 template <int NW>
-__device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> &T) {
-    for (int s = T.tid; s < C.K; s += T.NT)
+__device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> T) {
+    for (int s = T.tid(); s < C.K; s += T.NT)
         if (S.stop[s] == B) {
             const int c = child_of(S, B, s);
             if (c >= 0) S.stop[s] = c; else atomicOr(&S.ctr[C_ERR], ERR_INTERNAL);
         }
     T.sync();
-    if (T.tid == 0) {
+    if (T.tid() == 0) {
         const int m = S.clen[B], cb = S.cbeg[B];
         const int P = S.tpar[B], Cn = S.mate[B];
         const int xp = S.tps[B] >= 0 ? child_of(S, B, S.tps[B]) : -1;
@@ -1005,13 +1041,13 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         if (++C.events > C.max_events) return RUN_BUDGET;
         if (C.deadline && (C.events & 63) == 0) {
             int late = 0;
-            if (T.tid == 0) late = now_ns() > C.deadline;
+            if (T.tid() == 0) late = now_ns() > C.deadline;
             if (T.bcast(late)) return RUN_BUDGET;
         }
         unsigned long long best = EMPTY64;
         int flags = 0;   // bit 0: a growing region exists, bit 1: inconsistent state
         unsigned inner_leaf_min = INT_MAX;
-        for (int s = T.tid; s < C.K; s += T.NT) {
+        for (int s = T.tid(); s < C.K; s += T.NT) {
             // independent loads first, one dependent load (the label) after
             const int ip = S.inplay[s], A = S.stop[s], rad = S.srad[s], exh = S.sexh[s], sR = S.sR[s];
             const unsigned long long bb = ldr(&S.sbnd[s]);
@@ -1035,7 +1071,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             }
         }
         const int np = ldr(&S.ctr[C_NPAIRS]);
-        for (int i = T.tid; i < np; i += T.NT) {
+        for (int i = T.tid(); i < np; i += T.NT) {
             const int sl = S.plist[i];
             unsigned long long k;
             int pv;
@@ -1050,7 +1086,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             if (gap < 0 || gap % r) { flags |= 2; continue; }
             best = min(best, ev_key(C.t + gap / r, EV_COLLIDE, a, b));
         }
-        for (int v = C.K + T.tid; v < nhi; v += T.NT) {
+        for (int v = C.K + T.tid(); v < nhi; v += T.NT) {
             if (S.alive[v] && S.bpar[v] < 0 && S.label[v] == -1)
                 best = min(best, ev_key(C.t + S.y[v], EV_IMPLODE, S.minleaf[v], 0));
         }
@@ -1066,9 +1102,9 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         const int dt = (int)(tn - C.t);
         if ((unsigned)dt > inner_leaf_min) return RUN_INTERNAL;
         if (dt > 0) {
-            for (int v = T.tid; v < nhi; v += T.NT)
+            for (int v = T.tid(); v < nhi; v += T.NT)
                 if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0) S.y[v] += S.label[v] * dt;
-            for (int s = T.tid; s < C.K; s += T.NT)
+            for (int s = T.tid(); s < C.K; s += T.NT)
                 if (S.inplay[s]) S.srad[s] += S.label[S.stop[s]] * dt;
         }
         C.t = tn;
@@ -1082,9 +1118,9 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         T.sync();
         if (kind == EV_EXTEND) {
             // every growing region that reached its explored radius now
-            if (T.tid == 0) S.ctr[C_WL] = 0;
+            if (T.tid() == 0) S.ctr[C_WL] = 0;
             T.sync();
-            for (int s = T.tid; s < C.K; s += T.NT) {
+            for (int s = T.tid(); s < C.K; s += T.NT) {
                 const int rad = S.srad[s];
                 if (S.inplay[s] && !S.sexh[s] && S.label[S.stop[s]] == 1 && S.sR[s] - C.L + 1 - rad <= 0) {
                     const int k = atomicAdd(&S.ctr[C_WL], 1);
@@ -1114,7 +1150,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             if (act == 0) ev_blossom(S, C, A, a, B, b, T, nhi);
             else if (act == 1) ev_augment(S, C, A, a, B, b, T, nhi);
             else if (act == 2) {
-                if (T.tid == 0) ev_grow(S, A, a, B, b);
+                if (T.tid() == 0) ev_grow(S, A, a, B, b);
                 T.sync();
             } else {
                 return RUN_INTERNAL;
@@ -1147,7 +1183,7 @@ __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int
     for (int n = 0; n < 1 << 22 && cur != src; n++) {
         const int r0 = __ldg(g.row + cur), r1 = __ldg(g.row + cur + 1);
         unsigned long long best = EMPTY64;
-        for (int j = r0 + T.tid; j < r1; j += T.NT) {
+        for (int j = r0 + T.tid(); j < r1; j += T.NT) {
             SlotV sl = load_slot(g, j);
             if (sl.nbr < 0) continue;
             const int dy = ht_get(S, C, sl.nbr, s);
@@ -1155,7 +1191,7 @@ __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int
                 best = min(best, ((unsigned long long)(unsigned)__ldg(g.seid + j) << 32) | (unsigned)sl.nbr);
         }
         best = T.min64(best);
-        if (best == EMPTY64) { if (T.tid == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
+        if (best == EMPTY64) { if (T.tid() == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
         const int e = (int)(best >> 32);
         o ^= __ldg(g.eobs + e);
         cur = (int)(unsigned)(best & 0xffffffffu);
@@ -1168,14 +1204,14 @@ __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int
 // Expand the final matching into leaf-level pairs (tmpa[i], tmpb[i]; tmpb = -1
 // for a boundary match) and accumulate weight (internal units) and obs.
 template <int NW>
-__device__ __noinline__ void trace(const Slab &S, Shot &C, Team<NW> &T, int nhi, long long &wint,
+__device__ __noinline__ void trace(const Slab &S, Shot &C, Team<NW> T, int nhi, long long &wint,
                                    unsigned long long &obs) {
     // matched top-level nodes, team-parallel: each match appends its leaf pair
     // and queues the blossoms on either side for expansion (stack seeds)
-    if (T.tid == 0) { S.ctr[C_TNP] = 0; S.ctr[C_TNX] = 0; }
+    if (T.tid() == 0) { S.ctr[C_TNP] = 0; S.ctr[C_TNX] = 0; }
     T.sync();
     int *stk = S.stk;
-    for (int v = T.tid; v < nhi; v += T.NT) {
+    for (int v = T.tid(); v < nhi; v += T.NT) {
         if (!S.alive[v] || S.bpar[v] >= 0) continue;
         const int mt = S.mate[v];
         if (mt == MATE_BOUNDARY) {
@@ -1191,7 +1227,7 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, Team<NW> &T, int nhi,
     }
     T.sync();
     int np = ldr(&S.ctr[C_TNP]);
-    if (T.tid == 0) {
+    if (T.tid() == 0) {
         // blossoms: the child holding the externally matched leaf keeps that
         // match, the other children pair up along the cycle
         const int stk_cap = 4 * C.nc + 60;
@@ -1218,10 +1254,10 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, Team<NW> &T, int nhi,
     }
     np = T.bcast(np);
     T.sync();
-    if (T.tid == 0) S.ctr[C_TNP] = np;   // leaf pairs in tmpa / tmpb, read by commit_trace
+    if (T.tid() == 0) S.ctr[C_TNP] = np;   // leaf pairs in tmpa / tmpb, read by commit_trace
     long long w = 0;
     unsigned long long o = 0;
-    for (int i = T.tid; i < np; i += T.NT) {
+    for (int i = T.tid(); i < np; i += T.NT) {
         const int a = S.tmpa[i], b = S.tmpb[i];
         if (a < 0 || a >= C.K || b >= C.K) { set_err(S, ERR_INTERNAL); continue; }
         if (b < 0) {
@@ -1254,6 +1290,7 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, Team<NW> &T, int nhi,
     }
     wint = w;
     obs = o;
+    T.sync();
 }
 
 __device__ __forceinline__ bool in_commit(const DGraph &g, int v) {
@@ -1281,7 +1318,7 @@ __device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, 
     for (int n = 0; n < 1 << 22 && cur != src; n++) {
         const int r0 = __ldg(g.row + cur), r1 = __ldg(g.row + cur + 1);
         unsigned long long best = EMPTY64;
-        for (int j = r0 + T.tid; j < r1; j += T.NT) {
+        for (int j = r0 + T.tid(); j < r1; j += T.NT) {
             SlotV sl = load_slot(g, j);
             if (sl.nbr < 0) continue;
             const int dy = ht_get(S, C, sl.nbr, s);
@@ -1289,13 +1326,13 @@ __device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, 
                 best = min(best, ((unsigned long long)(unsigned)__ldg(g.seid + j) << 32) | (unsigned)sl.nbr);
         }
         best = T.min64(best);
-        if (best == EMPTY64) { if (T.tid == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
+        if (best == EMPTY64) { if (T.tid() == 0) S.ctr[C_ERR] |= ERR_INTERNAL; break; }
         const int e = (int)(best >> 32);
         const int nxt = (int)(unsigned)(best & 0xffffffffu);
         const bool ci = in_commit(g, cur), ni = in_commit(g, nxt);
         if (ci || ni) {
             o ^= __ldg(g.eobs + e);
-            if (ci != ni && T.tid == 0) {
+            if (ci != ni && T.tid() == 0) {
                 const int out = ci ? nxt : cur;
                 carry[out >> 5] ^= 1u << (out & 31);
             }
@@ -1314,9 +1351,9 @@ __device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, 
 // detectors outside the region flipped by committed edges.  Every thread of
 // the team calls.
 template <int NW>
-__device__ __noinline__ unsigned long long commit_trace(const Slab &S, Shot &C, Team<NW> &T, unsigned *carry) {
+__device__ __noinline__ unsigned long long commit_trace(const Slab &S, Shot &C, Team<NW> T, unsigned *carry) {
     const DGraph &g = C.g;
-    for (int w = T.tid; w < g.words; w += T.NT) carry[w] = 0u;
+    for (int w = T.tid(); w < g.words; w += T.NT) carry[w] = 0u;
     T.sync();
     const int np = T.bcast(ldr(&S.ctr[C_TNP]));
     unsigned long long o = 0;
@@ -1341,7 +1378,7 @@ __device__ __noinline__ unsigned long long commit_trace(const Slab &S, Shot &C, 
 // Per-shot counters; the tables themselves are already empty (release_tables).
 template <int NW>
 __device__ void clear_tables(const Slab &S, const Shot &C, Team<NW> &T) {
-    for (int i = T.tid; i < C_TOTAL; i += T.NT) S.ctr[i] = 0;
+    for (int i = T.tid(); i < C_TOTAL; i += T.NT) S.ctr[i] = 0;
     T.sync();
 }
 
@@ -1349,16 +1386,16 @@ __device__ void clear_tables(const Slab &S, const Shot &C, Team<NW> &T) {
 // lists (every explored entry) and the pair list (every pair), or with `all`
 // the whole region of this attempt's table sizes.
 template <int NW>
-__device__ __noinline__ void release_tables(const Slab &S, const Shot &C, Team<NW> &T, bool all) {
+__device__ __noinline__ void release_tables(const Slab &S, const Shot &C, Team<NW> T, bool all) {
     T.sync();
     const HEnt e = HEnt{EMPTY64, -1, -1};
     if (all) {
-        for (unsigned i = T.tid; i <= C.hmask; i += T.NT) S.ht[i] = e;
-        for (unsigned i = T.tid; i <= C.pmask; i += T.NT) S.pt[i] = e;
+        for (unsigned i = T.tid(); i <= C.hmask; i += T.NT) S.ht[i] = e;
+        for (unsigned i = T.tid(); i <= C.pmask; i += T.NT) S.pt[i] = e;
     } else {
         const int ne = ldr(&S.ctr[C_ECOUNT]), np = ldr(&S.ctr[C_NPAIRS]);
-        for (int i = T.tid; i < ne; i += T.NT) S.ht[S.ent[i] & C.hmask] = e;
-        for (int i = T.tid; i < np; i += T.NT) S.pt[S.plist[i] & C.pmask] = e;
+        for (int i = T.tid(); i < ne; i += T.NT) S.ht[S.ent[i] & C.hmask] = e;
+        for (int i = T.tid(); i < np; i += T.NT) S.pt[S.plist[i] & C.pmask] = e;
     }
     T.sync();
 }
@@ -1484,10 +1521,10 @@ __device__ __noinline__ int local_ball(const Slab &S, const Shot &C, int s, int 
 // prefix sum of the degrees; the warps of a team take 32 events each in turn.
 // Every thread of the team calls (no team barrier inside).
 template <int NW>
-__device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, const Team<NW> &T) {
+__device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, const Team<NW> T) {
     const DGraph &g = C.g;
     const int lane = T.lane;
-    for (int base = T.warp * WS; base < C.K; base += T.NT) {
+    for (int base = T.warp() * WS; base < C.K; base += T.NT) {
         const int s = base + lane;
         int src = -1, r0 = 0, deg = 0;
         if (s < C.K) {
@@ -1561,7 +1598,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     C.nm = 0; C.ncut = 0; C.tcut = 0; C.tlast = 0; C.nx = 0;
     if (g.words > A.caps.wcap) return -2;
     int K = 0;
-    if (T.warp == 0) K = load_defects(S, g, row, A.caps.kc, A.caps.wcap, T.lane);
+    if (T.warp() == 0) K = load_defects(S, g, row, A.caps.kc, A.caps.wcap, T.lane);
     K = T.bcast(K);
     T.sync();
     if (K < 0) return -2;
@@ -1569,9 +1606,9 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     C.max_events = min(A.max_events, 256LL * K + 4096);
     if (K == 0) {
         w_out = 0; o_out = 0;
-        if (dg && T.tid < QEC_DIAG_FIELDS) dg[T.tid] = 0;   // no detection event: E_ideal = 0
+        if (dg && T.tid() < QEC_DIAG_FIELDS) dg[T.tid()] = 0;   // no detection event: E_ideal = 0
         if constexpr (WIN)
-            for (int w = T.tid; w < g.words; w += T.NT) A.carry[(row - A.syn) + w] = 0u;
+            for (int w = T.tid(); w < g.words; w += T.NT) A.carry[(row - A.syn) + w] = 0u;
         return QEC_SHOT_OK;
     }
     if (K > ID_MAX - 1 || 2 * K + 8 > A.caps.nc) return -2;
@@ -1579,26 +1616,26 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     // about 8 (rarely ~15) explored entries and 1 (at most ~2) pair per
     // detection event at the design point; the tables stay at most half full or
     // the shot is retried with larger ones
-    const unsigned hs = min(next_pow2(max(128u, 32u * (unsigned)K * scale)), (unsigned)A.caps.hc);
+    const unsigned hs = min(next_pow2(max(128u, (unsigned)QEC_HT_FACTOR * (unsigned)K * scale)), (unsigned)A.caps.hc);
     const unsigned ps = min(next_pow2(max(64u, 4u * (unsigned)K * scale)), (unsigned)A.caps.phc);
     C.hmask = hs - 1;
     C.pmask = ps - 1;
     clear_tables(S, C, T);
     // sources, leaf nodes, free list
     int nhi = K;
-    for (int s = T.tid; s < K; s += T.NT) {
+    for (int s = T.tid(); s < K; s += T.NT) {
         S.srad[s] = 0; S.sR[s] = -1; S.scnt[s] = 0; S.sbeg[s] = 0; S.sexh[s] = 0; S.inplay[s] = 0;
         S.sbnd[s] = EMPTY64;
         S.alive[s] = 0; S.y[s] = 0; S.bpar[s] = -1; S.label[s] = 0; S.tpar[s] = -1;
         S.mate[s] = MATE_NONE; S.nroot[s] = -1; S.stop[s] = s; S.minleaf[s] = s; S.clen[s] = 0;
     }
     const int nfree = C.nc - K;
-    for (int i = T.tid; i < nfree; i += T.NT) {
+    for (int i = T.tid(); i < nfree; i += T.NT) {
         const int v = C.nc - 1 - i;   // pop order: K, K+1, ...
         S.freel[i] = v;
         S.alive[v] = 0; S.clen[v] = 0; S.bpar[v] = -1;
     }
-    if (T.tid == 0) { S.ctr[C_ECOUNT] = 0; S.ctr[C_NFREE] = nfree; }
+    if (T.tid() == 0) { S.ctr[C_ECOUNT] = 0; S.ctr[C_NFREE] = nfree; }
     T.sync();
     // level-1 critical path (stopping time, event count), clusters, events
     // resolved at level 1, events of all level-1 runs
@@ -1614,14 +1651,14 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         if (g.hop2) {
             level1_2hop(S, C, g.b1, T);
         } else {
-            for (int s = T.tid; s < K; s += T.NT) {
+            for (int s = T.tid(); s < K; s += T.NT) {
                 const int r = local_ball(S, C, s, g.b1);
                 if (r < 0) { S.cst0[s] = 1; any_big = true; } else S.cst0[s] = 0;
             }
         }
         T.sync();
         if (T.any(any_big)) {
-            if (T.tid == 0) {
+            if (T.tid() == 0) {
                 int k = 0;
                 for (int s = 0; s < K; s++)
                     if (S.cst0[s]) { S.xsrc[k] = s; S.xR[k] = max(g.b1, C.band); k++; }
@@ -1636,11 +1673,11 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         }
         const int npairs = T.bcast(ldr(&S.ctr[C_NPAIRS]));
         // connected components of pairs within b_1: min-label propagation
-        for (int s = T.tid; s < K; s += T.NT) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
+        for (int s = T.tid(); s < K; s += T.NT) { S.comp[s] = s; S.cst0[s] = 0; S.cst1[s] = 0; S.cst2[s] = 0; }
         T.sync();
         for (int round = 0; round <= K; round++) {
             bool changed = false;
-            for (int i = T.tid; i < npairs; i += T.NT) {
+            for (int i = T.tid(); i < npairs; i += T.NT) {
                 const int sl = S.plist[i];
                 unsigned long long k;
                 int pv;
@@ -1658,14 +1695,14 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
             T.sync();
             if (!T.any(changed)) break;
         }
-        for (int s = T.tid; s < K; s += T.NT) {
+        for (int s = T.tid(); s < K; s += T.NT) {
             const int r = S.comp[s];
             atomicAdd(&S.cst0[r], 1);
             const unsigned long long bb = S.sbnd[s];
             if (bb != EMPTY64 && 2LL * (long long)(bb >> 32) <= (long long)g.b1) atomicOr(&S.cst1[r], 1);
         }
         T.sync();
-        for (int i = T.tid; i < npairs; i += T.NT) {
+        for (int i = T.tid(); i < npairs; i += T.NT) {
             const int sl = S.plist[i];
             unsigned long long k;
             int pv;
@@ -1677,7 +1714,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         T.sync();
         // ---- level-1 clusters: closed forms for isolated pairs / boundary singletons
         bool need_general = false;
-        for (int s = T.tid; s < K; s += T.NT) {
+        for (int s = T.tid(); s < K; s += T.NT) {
             const int r = S.comp[s];
             const int size = S.cst0[r];
             const bool ok = (long long)S.cst2[r] == (long long)size * (size - 1) / 2 &&
@@ -1727,14 +1764,14 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         while (gr < K && (S.comp[gr] != gr || !(S.cst1[gr] & 2))) gr++;
         const bool top = gr >= K;
         if (top) {
-            for (int s = T.tid; s < K; s += T.NT) {
+            for (int s = T.tid(); s < K; s += T.NT) {
                 if (S.alive[s] || S.stop[s] != s) S.inplay[s] = 1;   // stopped level-1 configuration
                 else make_root(S, s);
             }
             C.ncut = 0;
             C.tcut = t1;
         } else {
-            for (int s = T.tid; s < K; s += T.NT)
+            for (int s = T.tid(); s < K; s += T.NT)
                 if (S.comp[s] == gr) make_root(S, s);
         }
         T.sync();
@@ -1747,7 +1784,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
                    : st == RUN_BUDGET ? QEC_SHOT_BUDGET_EXCEEDED : QEC_SHOT_INTERNAL;
         }
         if (top) break;
-        for (int s = T.tid; s < K; s += T.NT)
+        for (int s = T.tid(); s < K; s += T.NT)
             if (S.comp[s] == gr) S.inplay[s] = 0;
         T.sync();
         e1 = max(e1, C.nm); t1 = max(t1, C.tlast); ntot += C.nm; ncl1++; nres1 += S.cst0[gr];
@@ -1763,7 +1800,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     if (err) return (err & ERR_INTERNAL) ? QEC_SHOT_INTERNAL : -1;
     w_out = wint / 2;
     o_out = ob;
-    if (dg && T.tid == 0) {
+    if (dg && T.tid() == 0) {
         // parallel event count over level 1 and the top level (Methods,
         // "Numerical evaluation"): the top run's events up to the level-1
         // critical-path time t1 overlap level 1, the rest extend it
@@ -1813,23 +1850,23 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, T
     const bool retried = status < 0 && A.pass == 0 && A.single_shot < 0;   // goes to the overflow pass
     if (status < 0) {
         status = QEC_SHOT_CAPACITY;
-        if (retried && T.tid == 0) {
+        if (retried && T.tid() == 0) {
             const unsigned long long idx = atomicAdd(&A.queue[1], 1ull);
             A.overflow[idx] = (int)shot;
         }
         w = 0;
         o = 0;
     }
-    if (dg && status != QEC_SHOT_OK && T.tid < QEC_DIAG_FIELDS) dg[T.tid] = 0;
+    if (dg && status != QEC_SHOT_OK && T.tid() < QEC_DIAG_FIELDS) dg[T.tid()] = 0;
     if constexpr (WIN) {
         // sliding window: nothing is committed by a failed shot
         if (status != QEC_SHOT_OK)
-            for (int i = T.tid; i < g.words; i += T.NT) A.carry[off + i] = 0u;
-        if (T.tid == 0) {
+            for (int i = T.tid(); i < g.words; i += T.NT) A.carry[off + i] = 0u;
+        if (T.tid() == 0) {
             if (status == QEC_SHOT_OK) A.cobs[shot] ^= o;
             else if (!retried) A.st_out[shot] = status;
         }
-    } else if (T.tid == 0) {
+    } else if (T.tid() == 0) {
         A.w_out[shot] = w;
         A.obs_out[shot] = o;
         A.st_out[shot] = status;
@@ -1843,21 +1880,20 @@ template <bool WIN, int NW>
 __global__ void __launch_bounds__(NW == 1 ? 128 : 32 * NW, NW == 1 ? QEC_MIN_BLOCKS : 1)
 batch_kernel(const __grid_constant__ BatchArgs a) {
     Team<NW> T;
-    T.sh = nullptr;
+    T.lane = threadIdx.x & 31;
     if constexpr (NW > 1) {
         __shared__ TeamShared tsh;
         T.sh = &tsh;
+        T.tid_ = (int)threadIdx.x;
+        T.warp_ = (int)(threadIdx.x >> 5);
+        T.ph = 0;
     }
-    T.lane = threadIdx.x & 31;
-    T.tid = NW == 1 ? T.lane : (int)threadIdx.x;
-    T.warp = NW == 1 ? 0 : (int)(threadIdx.x >> 5);
-    T.ph = 0;
     const long long wid = NW == 1 ? (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) : (long long)blockIdx.x;
     Slab S;
     carve(a.slabs + wid * a.slab_bytes, a.caps, S);
     unsigned long long deadline = 0;
     if (a.watchdog_ns > 0) {
-        unsigned long long t0 = T.tid == 0 ? now_ns() : 0;
+        unsigned long long t0 = T.tid() == 0 ? now_ns() : 0;
         deadline = T.bcast64(t0) + (unsigned long long)a.watchdog_ns;
     }
     if (a.single_shot >= 0) {
@@ -1868,7 +1904,7 @@ batch_kernel(const __grid_constant__ BatchArgs a) {
     const long long limit = a.pass == 0 ? a.num_shots : (long long)min(a.queue[1], (unsigned long long)a.num_shots);
     for (long long it = 0; it < a.num_shots + 1; it++) {
         unsigned long long item = 0;
-        if (T.tid == 0) item = atomicAdd(counter, 1ull);
+        if (T.tid() == 0) item = atomicAdd(counter, 1ull);
         item = T.bcast64(item);
         if ((long long)item >= limit) break;
         const long long shot = a.pass == 0 ? (a.order ? (long long)a.order[item] : (long long)item)

@@ -7,7 +7,10 @@
 // appends the window to it.  A dispatcher thread launches the FILLING slot as
 // soon as fewer than N-1 slots are INFLIGHT (immediately when the GPU has room,
 // so a lone request is not held back), makes an IDLE slot the new FILLING one,
-// and turns finished slots into results with completion timestamps.
+// and turns finished slots into results with completion timestamps.  A
+// micro-batch small enough for one thread block per window is decoded by
+// multi-warp teams (a block of TEAM_BIG warps per window), which cuts the
+// latency of the large windows; larger micro-batches use one warp per window.
 
 #include <time.h>
 
@@ -71,6 +74,7 @@ struct qec_stream {
     long long cap_words = 0;
     int max_inflight = 0;
     int nwarps = 0, nwarps2 = 0;
+    int team_blocks = 0;   // resident blocks of the TEAM_BIG kernel on the device
     qec::SlabCaps caps{}, caps2{};
     long long sb = 0, sb2 = 0;
     std::vector<Slot> slots;
@@ -154,15 +158,27 @@ cudaError_t launch_slot(qec_stream *st, Slot &s) {
     a.slab_bytes = st->sb;
     a.caps = st->caps;
     a.pass = 0;
-    const int wpb = 4;
-    int warps = std::min(st->nwarps, (s.n + 0));
-    warps = (warps + wpb - 1) / wpb * wpb;
-    if ((e = qec::launch_batch(a, warps / wpb, 32 * wpb, s.cs))) return e;
+    // team size per window: set by qec_set_tuning, else a block of TEAM_BIG
+    // warps per window while the micro-batch has at most one window per
+    // available block (requests are latency-bound, the GPU has room to spare),
+    // one warp per window beyond that
+    const qec_tuning tune = qec::current_tuning();
+    int team = tune.team_warps;
+    if (team <= 0) team = s.n <= st->team_blocks ? qec::TEAM_BIG : 1;
+    if (team > 1) {
+        const int blocks = std::min(s.n, st->nwarps);
+        if ((e = qec::launch_batch(a, blocks, 32 * team, s.cs, team))) return e;
+    } else {
+        const int wpb = 4;
+        int warps = std::min(st->nwarps, (s.n + 0));
+        warps = (warps + wpb - 1) / wpb * wpb;
+        if ((e = qec::launch_batch(a, warps / wpb, 32 * wpb, s.cs))) return e;
+    }
     a.slabs = s.slabs2;
     a.slab_bytes = st->sb2;
     a.caps = st->caps2;
     a.pass = 1;
-    if ((e = qec::launch_batch(a, st->nwarps2, 32, s.cs))) return e;
+    if ((e = qec::launch_batch(a, st->nwarps2, team > 1 ? 32 * team : 32, s.cs, team))) return e;
     if ((e = cudaMemcpyAsync(s.h_obs, s.d_obs, (size_t)s.n * 8, cudaMemcpyDeviceToHost, s.cs))) return e;
     if ((e = cudaMemcpyAsync(s.h_w, s.d_w, (size_t)s.n * 8, cudaMemcpyDeviceToHost, s.cs))) return e;
     if ((e = cudaMemcpyAsync(s.h_st, s.d_st, (size_t)s.n * 4, cudaMemcpyDeviceToHost, s.cs))) return e;
@@ -249,6 +265,7 @@ int qec_stream_create(size_t device_budget_bytes, int32_t max_inflight, qec_stre
     st->max_inflight = max_inflight;
     st->nwarps = 2 * sms;
     st->nwarps2 = 16;
+    st->team_blocks = sms * qec::team_occupancy_blocks(qec::TEAM_BIG);
     st->caps = qec::caps_for_kcap(512, 1);
     st->caps2 = qec::caps_for_kcap(2048, 2);
     st->sb = qec::slab_bytes_for(st->caps);
