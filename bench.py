@@ -756,13 +756,13 @@ def scaling_line(q, args, dev):
     import torch
     out = {}
     checks = []
-    for d, n in ((25, 4000), (31, 3000), (41, 1500), (51, 800)):
+    for d, n in ((25, 4000), (31, 3000), (41, 2000), (51, 1200)):
         pg = rotated_surface_code(d, d, 0.003)
         syn, _ = sample_shots(pg, n, args.seed + 500 + d)
         K = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)
         g = q.Graph.from_phys(pg)
         t = torch.from_numpy(syn.view(np.int32).reshape(-1)).to(dev)
-        q.set_tuning(kcap=max(64, int(K.max() * 1.1) + 8), team_warps=1)
+        q.set_tuning(kcap=max(64, int(K.max() * 1.1) + 8), team_warps=-1)
         res = (torch.empty(n, dtype=torch.int64, device=dev), torch.empty(n, dtype=torch.int64, device=dev),
                torch.empty(n, dtype=torch.int32, device=dev))
         q.decode_batch([g], t, num_shots=n, out=res)
@@ -792,6 +792,7 @@ def scaling_line(q, args, dev):
             lat[team] = float(np.mean(times))
         out["d%d" % d] = {"d": d, "rounds": d, "p": 0.003, "windows": n, "mean_events": float(K.mean()),
                           "batched_windows_per_s": n / (ms / 1e3), "batched_us_per_round": ms * 1e3 / n / d,
+                          "batched_team_warps": "automatic",
                           "latency_us": lat[16] * 1e3, "latency_us_per_round": lat[16] * 1e3 / d,
                           "latency_team_warps": 16, "one_warp_latency_us": lat[1] * 1e3,
                           "team_speedup": lat[1] / lat[16],

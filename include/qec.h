@@ -300,9 +300,11 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
  * team_warps is the number of warps that decode one shot together: 1 = one warp
  * per shot (the throughput path: as many shots in flight as warps fit), 4 or
  * 16 = one thread block of that many warps per shot (every step of the shot
- * spread over the block: the latency path for large windows).  Automatic: 16
- * when a batch has fewer shots than the GPU has SMs and its largest graph has
- * at least team_min_detectors detectors, else 1.  Results do not depend on it. */
+ * spread over the block: the latency path for large windows).  Automatic, for
+ * a batch whose largest graph has at least team_min_detectors detectors: 16
+ * when the batch has at most one shot per SM, 4 while it has fewer shots than
+ * half the one-warp teams the GPU holds at once, else 1 (and always 1
+ * for smaller graphs).  Results do not depend on it. */
 typedef struct {
     int32_t warps_per_block;   /* 1 .. 32 */
     int32_t blocks_per_sm;     /* 1 .. 64 */

@@ -752,9 +752,19 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     if (bps <= 0) bps = qec::occupancy_blocks(32 * wpb);
     // team size: warps that decode one shot together (the sliding-window
     // kernel is compiled for one warp per shot only)
+    // automatic choice for a large graph: one 16-warp block per shot when the
+    // batch has at most one shot per SM, 4-warp blocks while it has fewer
+    // shots than half the resident one-warp teams (a shot per warp
+    // would leave most of the GPU idle), else one warp per shot
     int team = tune.team_warps;
-    if (team <= 0)
-        team = (!plain && num_shots < sms && nmax >= tune.team_min_detectors) ? qec::TEAM_BIG : 1;
+    if (team <= 0) {
+        team = 1;
+        if (!plain && nmax >= tune.team_min_detectors) {
+            const long long resident = (long long)sms * bps * wpb;
+            if (num_shots <= sms) team = qec::TEAM_BIG;
+            else if (num_shots * 2 < resident) team = qec::TEAM_MID;
+        }
+    }
     if (window) team = 1;
     // slabs: one per warp of the main pass (one warp per shot) or one per
     // resident block (one block per shot); the overflow pass has one per SM

@@ -1877,7 +1877,7 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, T
 // One team per warp (NW = 1, any block size that is a multiple of 32) or one
 // team per block (NW > 1, blocks of exactly 32 NW threads).
 template <bool WIN, int NW>
-__global__ void __launch_bounds__(NW == 1 ? 128 : 32 * NW, NW == 1 ? QEC_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(NW == 1 ? 128 : 32 * NW, NW == 1 ? QEC_MIN_BLOCKS : (NW == 4 ? 4 : 1))
 batch_kernel(const __grid_constant__ BatchArgs a) {
     Team<NW> T;
     T.lane = threadIdx.x & 31;
