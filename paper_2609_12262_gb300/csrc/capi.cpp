@@ -547,6 +547,7 @@ int qec_graph_create(const qec_graph_desc *desc, qec_graph **out) {
         long long wmin = LLONG_MAX;
         for (int e = 0; e < g->m; e++) wmin = std::min<long long>(wmin, g->ew[e]);
         d.hop2 = (g->m > 0 && 3 * wmin > (long long)d.b1) ? 1 : 0;
+        d.wmin = g->m > 0 ? (int)std::min<long long>(wmin, INT32_MAX / 4) : 1;
     }
     // Algorithm 1 above level 1: with one connected component and b_2 at least
     // the distance bound, every residual event links to every other at level

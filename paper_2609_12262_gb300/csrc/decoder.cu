@@ -86,7 +86,7 @@ constexpr long long T_MAX = (1LL << 26) - 1;
 enum { MATE_NONE = -1, MATE_BOUNDARY = -2 };
 
 // slab counters (C_R0 .. C_NEXT: work-list counters of multi-warp teams)
-enum { C_ECOUNT = 0, C_WL = 1, C_NPAIRS = 2, C_CCOUNT = 3, C_NFREE = 4, C_ERR = 5, C_HFILL = 6, C_NHI = 7,
+enum { C_ECOUNT = 0, C_WL = 1, C_NPAIRS = 2, C_CCOUNT = 3, C_NFREE = 4, C_ERR = 5, C_FRESH = 6, C_NHI = 7,
        C_TL = 8, C_CHANGED = 9, C_TNP = 10, C_TNX = 11, C_R0 = 12, C_NEXT = 15, C_TOTAL = 16 };
 enum { ERR_CAP = 1, ERR_INTERNAL = 2 };
 
@@ -573,16 +573,24 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
     const int lane = T.lane;
     T.sync();
     if (T.tid() == 0) {
-        S.ctr[C_TL] = 0; S.ctr[C_WL] = 0;
+        S.ctr[C_TL] = 0; S.ctr[C_WL] = 0; S.ctr[C_FRESH] = 0;
         if constexpr (NW > 1) { S.ctr[C_R0] = 0; S.ctr[C_R0 + 1] = 0; }
     }
     for (int i = T.tid(); i < nx; i += T.NT) { S.xcnt[i] = 0; S.xidx[S.xsrc[i]] = i; }
     T.sync();
     unsigned *F = reinterpret_cast<unsigned *>(S.wl0), *Wn = reinterpret_cast<unsigned *>(S.wl1);
-    // initial frontier: the previous band of every listed source; a source
-    // never explored so far starts from its own vertex at distance 0
+    // A source never explored whose target radius is below three smallest
+    // weights has a first ball made of paths of at most two edges: it is
+    // enumerated directly below (listed in xcur).  Initial frontier of the
+    // others: the previous band of every listed source; a source never
+    // explored so far starts from its own vertex at distance 0.
+    const int r3 = 3 * g.wmin;
     for (int i = T.tid(); i < nx; i += T.NT) {
         const int s = S.xsrc[i];
+        if (S.sR[s] < 0 && S.xR[i] < r3) {
+            S.xcur[atomicAdd(&S.ctr[C_FRESH], 1)] = i;
+            continue;
+        }
         if (S.sR[s] < 0) {
             unsigned hs;
             const int r = ht_upsert(S, C, S.svtx[s], s, 0, hs);
@@ -610,6 +618,96 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
     // three slots (a slot is cleared two rounds before its next use)
     int ntl = ldr(&S.ctr[C_TL]);
     const unsigned lt = (1u << lane) - 1u;
+    // new explored entry (table slot hs) of list position xi: one slot in `tl`
+    // per inserted entry, placed by ballot (one warp) or by one atomic per warp
+    auto append_tl = [&](bool ins, unsigned hs, int xi) {
+        const unsigned mt = __ballot_sync(FULL, ins);
+        int bt;
+        if constexpr (NW == 1) {
+            bt = ntl;
+            ntl += __popc(mt);
+        } else {
+            bt = 0;
+            if (lane == 0 && mt) bt = atomicAdd(&S.ctr[C_TL], __popc(mt));
+            bt = __shfl_sync(FULL, bt, 0);
+        }
+        if (ins) {
+            const int e = bt + __popc(mt & lt);
+            if (e < C.ec) S.tl[e] = ((unsigned long long)hs << 32) | (unsigned)xi; else set_err(S, ERR_CAP);
+        }
+    };
+    {
+        // first balls by enumeration: every vertex within radius R of the
+        // source is reached by a path of one or two edges, so the minimum over
+        // those paths is its exact distance; boundary candidates through the
+        // source and its neighbours (the band's farther vertices are the next
+        // extension's frontier, which adds theirs before a region can get
+        // there).  One lane per (source, adjacency slot), as in level1_2hop.
+        const int nfr = ldr(&S.ctr[C_FRESH]);
+        for (int base = T.warp() * WS; base < nfr; base += T.NT) {
+            const int idx = base + lane;
+            int src = -1, r0 = 0, deg = 0, xi = 0, s = 0, R = -1;
+            bool ins = false;
+            unsigned hs = 0;
+            if (idx < nfr) {
+                xi = S.xcur[idx];
+                s = S.xsrc[xi];
+                R = S.xR[xi];
+                src = S.svtx[s];
+                r0 = __ldg(g.row + src);
+                deg = __ldg(g.row + src + 1) - r0;
+                ins = ht_upsert(S, C, src, s, 0, hs) == 1;
+            }
+            append_tl(ins, hs, xi);
+            int incl = deg;
+            for (int o = 1; o < WS; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(FULL, incl, WS - 1);
+            const int excl = incl - deg;
+            for (int t0 = 0; t0 < total; t0 += WS) {
+                const int t = t0 + lane;
+                int ow = 0;
+                for (int step = WS / 2; step > 0; step >>= 1) {
+                    const int e = __shfl_sync(FULL, excl, ow + step);
+                    if (e <= t) ow += step;
+                }
+                const int osrc = __shfl_sync(FULL, src, ow);
+                const int oj = __shfl_sync(FULL, r0 - excl, ow) + t;
+                const int os = __shfl_sync(FULL, s, ow);
+                const int oR = __shfl_sync(FULL, R, ow);
+                const int oxi = __shfl_sync(FULL, xi, ow);
+                int an = -1, aw = 0;
+                bool ins1 = false;
+                unsigned h1 = 0;
+                if (t < total) {
+                    const SlotV a = load_slot(g, oj);
+                    aw = a.w;
+                    if (a.nbr < 0) bnd_update(S, os, a.w, a.eid);
+                    else if (a.w <= oR) {
+                        an = a.nbr;
+                        ins1 = ht_upsert(S, C, an, os, a.w, h1) == 1;
+                    }
+                }
+                append_tl(ins1, h1, oxi);
+                // second edges from the neighbour, one lane each
+                const int q0 = an >= 0 ? __ldg(g.row + an) : 0, q1 = an >= 0 ? __ldg(g.row + an + 1) : 0;
+                const int nq = __reduce_max_sync(FULL, (unsigned)(q1 - q0));
+                for (int k = 0; k < nq; k++) {
+                    bool ins2 = false;
+                    unsigned h2 = 0;
+                    if (k < q1 - q0) {
+                        const SlotV b = load_slot(g, q0 + k);
+                        const int nd = aw + b.w;
+                        if (b.nbr < 0) bnd_update(S, os, nd, b.eid);
+                        else if (nd <= oR && b.nbr != osrc) ins2 = ht_upsert(S, C, b.nbr, os, nd, h2) == 1;
+                    }
+                    append_tl(ins2, h2, oxi);
+                }
+            }
+        }
+    }
     for (int iter = 0;; iter++) {
         if (iter >= 4096) { if (T.tid() == 0) set_err(S, ERR_INTERNAL); break; }
         int nwl = 0;

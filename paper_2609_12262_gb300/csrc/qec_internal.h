@@ -26,7 +26,7 @@ struct DGraph {
     int d1, b1;        // Algorithm 3 level-1 diameter / buffer (internal units)
     int internal_obs;  // some detector-detector edge carries an observable
     int hop2;          // 3 x smallest internal weight > b1: a path of length <= b1 has at most two edges
-    int pad1;
+    int wmin;          // smallest internal weight
     const int *row;                   // [n + 1]
     const Slot *slot;                 // [row[n]]
     const unsigned long long *eobs;   // [merged edges]
