@@ -752,7 +752,7 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     int bps = tune.blocks_per_sm;
     if (bps <= 0) bps = qec::occupancy_blocks(32 * wpb);
     // team size: warps that decode one shot together (the sliding-window
-    // kernel is compiled for one warp per shot only)
+    // kernel is compiled for one warp and for TEAM_BIG warps per shot)
     // automatic choice for a large graph: one 16-warp block per shot when the
     // batch has at most one shot per SM, 4-warp blocks while it has fewer
     // shots than half the resident one-warp teams (a shot per warp
@@ -766,7 +766,7 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
             else if (num_shots * 2 < resident) team = qec::TEAM_MID;
         }
     }
-    if (window) team = 1;
+    if (window && team == qec::TEAM_MID) team = 1;
     // slabs: one per warp of the main pass (one warp per shot) or one per
     // resident block (one block per shot); the overflow pass has one per SM
     long long nwarps = plain ? 1 : (long long)sms * bps * wpb;

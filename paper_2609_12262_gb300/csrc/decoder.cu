@@ -35,8 +35,8 @@
 //   5. Tracing: blossoms are expanded into matched event pairs and boundary
 //      matches; the weight is the sum of the tight pair / boundary distances and
 //      the observable mask the XOR of the canonical paths' masks.  The
-//      sliding-window instantiation (batch_kernel<true, 1>) also walks every
-//      path and commits the edges that touch the window's commit region.
+//      sliding-window instantiations (batch_kernel<true, *>) also walk every
+//      path and commit the edges that touch the window's commit region.
 //
 // Simultaneous events are applied in the canonical order (t, kind, lo, hi) with
 // kind EXTEND < IMPLODE < COLLIDE < BOUNDARY and lo, hi the ranks of the events
@@ -2086,7 +2086,8 @@ SlabCaps caps_for_kcap(int kcap, int table_factor) {
 
 cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s, int team) {
     if (a.carry) {
-        batch_kernel<true, 1><<<grid, block, 0, s>>>(a);
+        if (team == TEAM_BIG) batch_kernel<true, TEAM_BIG><<<grid, 32 * TEAM_BIG, 0, s>>>(a);
+        else batch_kernel<true, 1><<<grid, block, 0, s>>>(a);
     } else if (team == TEAM_BIG) {
         batch_kernel<false, TEAM_BIG><<<grid, 32 * TEAM_BIG, 0, s>>>(a);
     } else if (team == TEAM_MID) {

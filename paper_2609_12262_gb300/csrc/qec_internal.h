@@ -87,7 +87,8 @@ SlabCaps caps_for_kcap(int kcap, int table_factor = 1);
 constexpr int TEAM_MID = 4;
 constexpr int TEAM_BIG = 16;
 // Launch the batch kernel: team 1 = one warp per shot (grid x block threads),
-// TEAM_MID / TEAM_BIG = one block of that many warps per shot (grid blocks).
+// TEAM_MID / TEAM_BIG = one block of that many warps per shot (grid blocks);
+// sliding-window batches (a.carry set) take team 1 or TEAM_BIG.
 cudaError_t launch_batch(const BatchArgs &a, int grid, int block, cudaStream_t s, int team = 1);
 // Resident blocks per SM of the multi-warp batch kernel of team size `team`.
 int team_occupancy_blocks(int team);

@@ -147,3 +147,23 @@ def test_team_large_windows(qd, d, p, shots):
     gpu = (np.concatenate([x[0].cpu().numpy() for x in outs]), np.concatenate([qd.to_uint64(x[1]) for x in outs]),
            np.concatenate([x[2].cpu().numpy() for x in outs]))
     assert_same(gpu, ref, "d%d p%g single windows" % (d, p))
+
+
+@pytest.mark.parametrize("team", [1, 16])
+def test_team_sliding_windows(qd, team):
+    """Sliding-window decoding (committed paths and carries) with one warp and
+    with a 16-warp block per stream window, against the oracle's windows."""
+    import torch
+    from oracle.window import sliding_window_decode
+    from paper_2609_12262_gb300.window import SlidingWindow
+    from synth import rotated_surface_code_circuit
+    for g, W, C, S in ((rotated_surface_code(7, 28, 0.006), 14, 7, 60),
+                       (rotated_surface_code_circuit(5, 15, 0.004), 6, 3, 40)):
+        syn, _ = sample_shots(g, S, 29)
+        dec = SlidingWindow(qd.Graph.from_phys(g), g.nz, W, C)
+        t = torch.from_numpy(syn.view(np.int32).reshape(-1)).cuda()
+        obs, st = with_team(qd, team, dec.decode, t, S)
+        torch.cuda.synchronize()
+        ro, rs = sliding_window_decode(g, syn, W, C)
+        assert not rs.any()
+        assert np.array_equal(qd.to_uint64(obs), ro) and np.array_equal(st.cpu().numpy(), rs), team
