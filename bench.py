@@ -754,8 +754,20 @@ def scaling_line(q, args, dev):
     latency of one window decoded alone (a 16-warp team per window, and one
     warp for comparison); the single windows are checked against the oracle."""
     import torch
+    from paper_2609_12262_gb300 import autotune
     out = {}
     checks = []
+    # split threshold of the 16-warp teams (windows with fewer detection events
+    # go to one warp), tuned on two windows of each distance at p = 0.001 and
+    # 0.003 (other seeds than the measured windows)
+    samples = []
+    for d in (25, 31, 41, 51):
+        for p in (0.001, 0.003):
+            pg = rotated_surface_code(d, d, p)
+            sy, _ = sample_shots(pg, 2, args.seed + 700 + d + int(p * 1e4))
+            samples.append((q.Graph.from_phys(pg), torch.from_numpy(sy.view(np.int32).reshape(-1)).to(dev)))
+    split, split_totals = autotune.tune_split(samples, reps=1)
+    out["team_split_events"] = {"chosen": split, "total_ms": {str(sp): ms for ms, sp in split_totals}}
     for d, n in ((25, 4000), (31, 3000), (41, 2000), (51, 1200)):
         pg = rotated_surface_code(d, d, 0.003)
         syn, _ = sample_shots(pg, n, args.seed + 500 + d)
@@ -776,7 +788,7 @@ def scaling_line(q, args, dev):
         lat = {}
         one = []
         for team in (16, 1):
-            q.set_tuning(team_warps=team)
+            q.set_tuning(team_warps=team, team_split_events=split)
             times = []
             for s in range(-1, 6):
                 k = max(s, 0)

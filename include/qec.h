@@ -294,7 +294,7 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
  * a knob, zero keeps its current value and a negative value restores the
  * default (warps_per_block 4, blocks_per_sm 0 = as many as fit, band_factor 1,
  * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, max_events 4e6,
- * team_warps 0 = automatic, team_min_detectors 2048).
+ * team_warps 0 = automatic, team_min_detectors 2048, team_split_events 64).
  * qec_get_tuning reports 0 for the automatic choices.
  *
  * team_warps is the number of warps that decode one shot together: 1 = one warp
@@ -313,6 +313,8 @@ typedef struct {
     int64_t max_events;        /* event budget per shot */
     int32_t team_warps;        /* 1, 4 or 16; 0 = automatic */
     int32_t team_min_detectors;   /* automatic team choice: smallest graph for a block per shot */
+    int32_t team_split_events; /* a block decodes a shot with fewer detection events than
+                                * this with its first warp alone (1: never) */
 } qec_tuning;
 int qec_set_tuning(const qec_tuning *t);
 int qec_get_tuning(qec_tuning *t);

@@ -50,7 +50,7 @@ class qec_graph_info(C.Structure):
 class qec_tuning(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("band_factor", C.c_int32),
                 ("kcap", C.c_int32), ("max_events", C.c_int64), ("team_warps", C.c_int32),
-                ("team_min_detectors", C.c_int32)]
+                ("team_min_detectors", C.c_int32), ("team_split_events", C.c_int32)]
 
 
 class qec_result(C.Structure):
@@ -419,10 +419,10 @@ class Stream:
 
 
 def set_tuning(warps_per_block=0, blocks_per_sm=0, band_factor=0, kcap=0, max_events=0, team_warps=0,
-               team_min_detectors=0):
+               team_min_detectors=0, team_split_events=0):
     """qec_set_tuning: positive sets a knob, 0 keeps it, negative restores its default."""
     t = qec_tuning(int(warps_per_block), int(blocks_per_sm), int(band_factor), int(kcap), int(max_events),
-                   int(team_warps), int(team_min_detectors))
+                   int(team_warps), int(team_min_detectors), int(team_split_events))
     _check(lib().qec_set_tuning(C.byref(t)))
 
 

@@ -1,10 +1,13 @@
-"""Autotuner for the batched decoder's launch shape and per-warp slab sizes.
+"""Autotuner for the batched decoder's launch shape, per-warp slab sizes and
+the team split threshold.
 
-It times qec_decode_batch on a sample of the caller's own workload for every
-candidate (warps per block, resident blocks per SM, flooder band width, slab
-capacity), requires every candidate to return exactly the same weights,
+tune() times qec_decode_batch on a sample of the caller's own workload for
+every candidate (warps per block, resident blocks per SM, flooder band width,
+slab capacity), requires every candidate to return exactly the same weights,
 observables and statuses as the first one (tuning never changes results), and
 stores the fastest in a JSON cache keyed by GPU name and graph set.
+tune_split() chooses, for single windows decoded by a 16-warp block, the
+detection-event count below which the block's first warp decodes alone.
 """
 
 from __future__ import annotations
@@ -105,3 +108,45 @@ def tune(graphs, syn, graph_of_shot, offsets, reps: int = 2, budget_s: float = 6
         with open(CACHE, "w") as f:
             json.dump(db, f, indent=1)
     return best, results
+
+
+def tune_split(samples, splits=(1, 24, 48, 64, 96, 128, 192), team: int = 16, reps: int = 2):
+    """Choose the team split threshold for single-window decoding: a block of
+    `team` warps hands a window with fewer detection events than the threshold
+    to its first warp.  `samples` is a list of (Graph, int32 device tensor of
+    one or more syndrome rows); every window is decoded alone (one launch per
+    window) for every candidate, the results must agree across candidates,
+    and the threshold with the smallest total latency is applied and returned
+    with the per-candidate totals (ms)."""
+    import torch
+    saved = get_tuning()
+    ref = None
+    totals = []
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        for sp in splits:
+            set_tuning(team_warps=team, team_split_events=sp)
+            got, ms = [], 0.0
+            for g, rows in samples:
+                n = rows.numel() // g.words
+                for k in range(n):
+                    one = rows[k * g.words:(k + 1) * g.words]
+                    decode_batch([g], one, num_shots=1)   # warm
+                    for _ in range(reps):
+                        a.record()
+                        o, w, st = decode_batch([g], one, num_shots=1)
+                        b.record()
+                        torch.cuda.synchronize()
+                        ms += a.elapsed_time(b) / reps
+                    got.append((int(w.item()), int(o.item()), int(st.item())))
+            if ref is None:
+                ref = got
+            elif got != ref:
+                raise RuntimeError("split threshold %d changed the decoding result" % sp)
+            totals.append((ms, sp))
+    finally:
+        set_tuning(**{k: _v(v) for k, v in saved.items()})
+    totals.sort()
+    best = totals[0][1]
+    set_tuning(team_split_events=best)
+    return best, totals

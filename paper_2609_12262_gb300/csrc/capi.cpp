@@ -288,7 +288,7 @@ struct Workspace {
 
 Workspace g_ws[64];
 std::mutex g_tune_mu;
-qec_tuning g_tune = {4, 0, 1, 0, 4000000, 0, 2048};
+qec_tuning g_tune = {4, 0, 1, 0, 4000000, 0, 2048, 64};
 
 void ws_free(Workspace &w) {
     if (w.slabs) cudaFree(w.slabs);
@@ -678,7 +678,7 @@ int qec_set_tuning(const qec_tuning *t) {
         return fail(QEC_EINVAL, "tuning value out of range");
     if (t->team_warps > 0 && t->team_warps != 1 && t->team_warps != qec::TEAM_MID && t->team_warps != qec::TEAM_BIG)
         return fail(QEC_EINVAL, "team_warps must be 1, 4 or 16 (0 keeps, negative = automatic)");
-    static const qec_tuning defaults = {4, 0, 1, 0, 4000000, 0, 2048};
+    static const qec_tuning defaults = {4, 0, 1, 0, 4000000, 0, 2048, 64};
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto pick = [](auto v, auto cur, auto def) { return v > 0 ? v : (v < 0 ? def : cur); };
     g_tune.warps_per_block = pick(t->warps_per_block, g_tune.warps_per_block, defaults.warps_per_block);
@@ -688,6 +688,9 @@ int qec_set_tuning(const qec_tuning *t) {
     g_tune.max_events = pick(t->max_events, g_tune.max_events, defaults.max_events);
     g_tune.team_warps = pick(t->team_warps, g_tune.team_warps, defaults.team_warps);
     g_tune.team_min_detectors = pick(t->team_min_detectors, g_tune.team_min_detectors, defaults.team_min_detectors);
+    // team_split_events: 0 keeps, negative restores the default, and a value
+    // of 1 means every shot goes to the whole team
+    g_tune.team_split_events = pick(t->team_split_events, g_tune.team_split_events, defaults.team_split_events);
     return QEC_OK;
 }
 
@@ -813,6 +816,7 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     a.diag_out = diag_out;
     a.cobs = reinterpret_cast<unsigned long long *>(commit_obs);
     a.carry = carry_out;
+    a.team_split = tune.team_split_events;
     if (plain) {
         a.slabs = w.slabs;
         a.slab_bytes = w.slab_bytes;

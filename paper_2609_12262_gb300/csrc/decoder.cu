@@ -1931,6 +1931,19 @@ __device__ int decode_attempt(const BatchArgs &A, const Slab &S, const DGraph &g
     return st;
 }
 
+// Detection events of a syndrome row (padding bits beyond n ignored).  One warp.
+__device__ int count_defects(const DGraph &g, const unsigned *row, int lane) {
+    int c = 0;
+    for (int w = lane; w < g.words; w += WS) {
+        unsigned v = __ldg(row + w);
+        const int bit0 = w * 32;
+        if (bit0 >= g.n) v = 0;
+        else if (bit0 + 32 > g.n) v &= (1u << (g.n - bit0)) - 1u;
+        c += __popc(v);
+    }
+    return (int)__reduce_add_sync(FULL, (unsigned)c);
+}
+
 template <bool WIN, int NW>
 __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, Team<NW> &T,
                             unsigned long long deadline) {
@@ -1939,6 +1952,24 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, T
     const DGraph &g = A.g[gi];
     const long long off = A.syn_off ? A.syn_off[shot] : shot * (long long)g.words;
     const unsigned *row = A.syn + off;
+    if constexpr (NW > 1) {
+        // a shot below the split threshold goes to the team's first warp
+        // alone (a team's barriers cost more than its lanes save there)
+        if (A.team_split > 0) {
+            int K = 0;
+            if (T.warp() == 0) K = count_defects(g, row, T.lane);
+            K = T.bcast(K);
+            if (K < A.team_split) {
+                if (T.warp() == 0) {
+                    Team<1> T1;
+                    T1.lane = T.lane;
+                    decode_shot<WIN, 1>(A, S, shot, T1, deadline);
+                }
+                T.sync();
+                return;
+            }
+        }
+    }
     int status = -1;
     long long w = 0;
     unsigned long long o = 0;

@@ -76,6 +76,9 @@ struct BatchArgs {
     // change to a failure, and obs_out / w_out are not written
     unsigned long long *cobs;
     unsigned *carry;
+    // multi-warp teams: a shot with fewer detection events than this is
+    // decoded by the team's first warp alone (0: always by the whole team)
+    int team_split;
 };
 
 long long slab_bytes_for(const SlabCaps &c);

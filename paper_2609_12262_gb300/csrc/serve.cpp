@@ -163,6 +163,7 @@ cudaError_t launch_slot(qec_stream *st, Slot &s) {
     // available block (requests are latency-bound, the GPU has room to spare),
     // one warp per window beyond that
     const qec_tuning tune = qec::current_tuning();
+    a.team_split = tune.team_split_events;
     int team = tune.team_warps;
     if (team <= 0) team = s.n <= st->team_blocks ? qec::TEAM_BIG : 1;
     if (team > 1) {

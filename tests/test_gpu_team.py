@@ -25,15 +25,17 @@ def qd():
     import paper_2609_12262_gb300 as q
     q.lib()
     yield q
-    q.set_tuning(team_warps=-1, kcap=-1)
+    q.set_tuning(team_warps=-1, kcap=-1, team_split_events=-1)
 
 
-def with_team(q, team, fn, *a, **kw):
-    q.set_tuning(team_warps=team)
+def with_team(q, team, fn, *a, split=1, **kw):
+    """Run fn with team_warps = team; split = 1 sends every shot to the whole
+    team (the default threshold would give small shots to one warp)."""
+    q.set_tuning(team_warps=team, team_split_events=split)
     try:
         return fn(*a, **kw)
     finally:
-        q.set_tuning(team_warps=-1)
+        q.set_tuning(team_warps=-1, team_split_events=-1)
 
 
 CASES = [
@@ -167,3 +169,18 @@ def test_team_sliding_windows(qd, team):
         ro, rs = sliding_window_decode(g, syn, W, C)
         assert not rs.any()
         assert np.array_equal(qd.to_uint64(obs), ro) and np.array_equal(st.cpu().numpy(), rs), team
+
+
+def test_team_split_threshold(qd):
+    """A 16-warp block hands shots below the split threshold to its first warp:
+    results equal the oracle whatever the threshold, and the shots on either
+    side of it are both present in the batch."""
+    graphs, gid, offs, syn = mixed_batch([9, 17, 25], 40, 0.004, seed=17)
+    gg = [qd.Graph.from_phys(pg) for pg in graphs]
+    rows = [syn[offs[s]:offs[s] + graphs[gid[s]].words] for s in range(gid.shape[0])]
+    K = np.array([np.unpackbits(np.asarray(r, np.uint32).view(np.uint8)).sum() for r in rows])
+    assert np.count_nonzero(K < 40) >= 20 and np.count_nonzero(K >= 40) >= 20
+    ref = oracle_decode(graphs, gid, rows)
+    for split in (1, 40, 100000):
+        gpu = with_team(qd, 16, gpu_decode, qd, gg, (syn, offs), gid=gid, split=split)
+        assert_same(gpu, ref, "split %d" % split)
