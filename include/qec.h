@@ -294,7 +294,9 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
  * a knob, zero keeps its current value and a negative value restores the
  * default (warps_per_block 4, blocks_per_sm 0 = as many as fit, band_factor 1,
  * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, max_events 4e6,
- * team_warps 0 = automatic, team_min_detectors 2048, team_split_events 64).
+ * team_warps 0 = automatic, team_min_detectors 2048, team_split_events 1:
+ * every shot of a block goes to the whole block; on a GB300 the autotuner's
+ * split search found no threshold faster than that for single windows).
  * qec_get_tuning reports 0 for the automatic choices.
  *
  * team_warps is the number of warps that decode one shot together: 1 = one warp

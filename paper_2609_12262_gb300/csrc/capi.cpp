@@ -288,7 +288,7 @@ struct Workspace {
 
 Workspace g_ws[64];
 std::mutex g_tune_mu;
-qec_tuning g_tune = {4, 0, 1, 0, 4000000, 0, 2048, 64};
+qec_tuning g_tune = {4, 0, 1, 0, 4000000, 0, 2048, 1};
 
 void ws_free(Workspace &w) {
     if (w.slabs) cudaFree(w.slabs);
@@ -678,7 +678,7 @@ int qec_set_tuning(const qec_tuning *t) {
         return fail(QEC_EINVAL, "tuning value out of range");
     if (t->team_warps > 0 && t->team_warps != 1 && t->team_warps != qec::TEAM_MID && t->team_warps != qec::TEAM_BIG)
         return fail(QEC_EINVAL, "team_warps must be 1, 4 or 16 (0 keeps, negative = automatic)");
-    static const qec_tuning defaults = {4, 0, 1, 0, 4000000, 0, 2048, 64};
+    static const qec_tuning defaults = {4, 0, 1, 0, 4000000, 0, 2048, 1};
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto pick = [](auto v, auto cur, auto def) { return v > 0 ? v : (v < 0 ? def : cur); };
     g_tune.warps_per_block = pick(t->warps_per_block, g_tune.warps_per_block, defaults.warps_per_block);
