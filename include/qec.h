@@ -176,7 +176,16 @@ int qec_graph_merged_edges(const qec_graph *g, int32_t *u, int32_t *v, int32_t *
  * initialised by one asynchronous fill on `stream`); calls that share the
  * workspace are serialised on their streams by the library.  Errors: QEC_EINVAL (null
  * output pointers, num_graphs out of range, graphs on another device),
- * QEC_ENOMEM, QEC_ECUDA. num_shots == 0 is a no-op. */
+ * QEC_ENOMEM, QEC_ECUDA. num_shots == 0 is a no-op.
+ *
+ * CUDA graphs: a call on a stream that is capturing is recorded into the
+ * caller's graph (kernel arguments, shot count and the current tuning are
+ * fixed at capture).  It needs a call of the same shape (graphs, shot count,
+ * tuning) made before outside capture, which sizes and fills the workspace;
+ * otherwise it returns QEC_EINVAL.  Captured work does not take part in the
+ * library's ordering of workspace users: replays of the graph must not overlap
+ * other decodes on the same device.  The same holds for qec_decode_batch_ex
+ * and qec_decode_window_batch. */
 int qec_decode_batch(const qec_graph *const *graphs, int32_t num_graphs,
                      const int32_t *graph_of_shot, const int64_t *syn_offset_words,
                      const uint32_t *syndromes, int64_t num_shots,

@@ -316,10 +316,22 @@ int kcap_for(int nmax, const qec_tuning &t) {
     return std::min(k, std::max(nmax, 1));
 }
 
+// Every capacity of `have` at least that of `need`: a slab laid out for
+// `have` serves the request (capacities change no result, only which shots
+// run out of room).
+bool caps_cover(const SlabCaps &have, const SlabCaps &need) {
+    return have.kc >= need.kc && have.hc >= need.hc && have.ec >= need.ec && have.wc >= need.wc &&
+           have.phc >= need.phc && have.nc >= need.nc && have.cc >= need.cc && have.wcap >= need.wcap;
+}
+
 // Make sure the workspace of `dev` fits the request; may synchronise the device.
-int ws_ensure(Workspace &w, int dev, const SlabCaps &caps, long long nwarps, const SlabCaps &caps2,
-              long long nwarps2, long long nshots) {
+// A slab layout that already covers the request is kept as it is (no new
+// allocation and no refill), so alternating batch shapes reuse the largest.
+int ws_ensure(Workspace &w, int dev, SlabCaps caps, long long nwarps, SlabCaps caps2, long long nwarps2,
+              long long nshots) {
     w.device = dev;
+    if (w.slabs && nwarps <= w.nwarps && caps_cover(w.caps, caps)) caps = w.caps;
+    if (w.slabs2 && nwarps2 <= w.nwarps2 && caps_cover(w.caps2, caps2)) caps2 = w.caps2;
     const long long sb = qec::slab_bytes_for(caps);
     const long long sb2 = qec::slab_bytes_for(caps2);
     cudaError_t e;
@@ -375,6 +387,16 @@ int ws_ensure(Workspace &w, int dev, const SlabCaps &caps, long long nwarps, con
         w.overflow_cap = cap;
     }
     return QEC_OK;
+}
+
+// Whether the workspace already holds this request as it stands (no growth,
+// same slab layouts, nothing left to fill): the condition for decoding inside
+// a stream capture, where nothing may be allocated or synchronised.
+bool ws_fits(const Workspace &w, const SlabCaps &caps, long long nwarps, const SlabCaps &caps2, long long nwarps2,
+             long long nshots) {
+    if (!w.done || !w.queue || !w.slabs || !w.slabs2 || w.fill1 || w.fill2) return false;
+    if (nwarps > w.nwarps || nwarps2 > w.nwarps2 || nshots > w.overflow_cap) return false;
+    return caps_cover(w.caps, caps) && caps_cover(w.caps2, caps2);
 }
 
 int sm_count(int dev) {
@@ -782,10 +804,23 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     if (plain) caps = caps2;
     Workspace &w = g_ws[dev];
     std::lock_guard<std::mutex> lk(w.mu);
-    int rc = ws_ensure(w, dev, caps, nwarps, caps2, nwarps2, plain ? 1 : num_shots);
-    if (rc != QEC_OK) return rc;
-    ce = cudaStreamWaitEvent(s, w.done, 0);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamWaitEvent");
+    // inside a stream capture the workspace must already fit (a call of the
+    // same shape outside capture sizes and fills it), and the workspace event
+    // is neither waited on nor recorded: the captured graph's replays are
+    // ordered by the caller
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    if (capturing) {
+        if (!ws_fits(w, caps, nwarps, caps2, nwarps2, plain ? 1 : num_shots))
+            return fail(QEC_EINVAL, "stream capture needs a prior uncaptured call of the same shape (workspace not ready)");
+    } else {
+        int rc = ws_ensure(w, dev, caps, nwarps, caps2, nwarps2, plain ? 1 : num_shots);
+        if (rc != QEC_OK) return rc;
+        ce = cudaStreamWaitEvent(s, w.done, 0);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamWaitEvent");
+    }
     if (w.fill1) {
         ce = cudaMemsetAsync(w.slabs, 0xff, (size_t)(w.slab_bytes * w.nwarps), s);
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaMemsetAsync");
@@ -856,8 +891,10 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
         ce = qec::launch_batch(a, (int)nwarps2, team > 1 ? 32 * team : 32, s, team);
         if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
     }
-    ce = cudaEventRecord(w.done, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventRecord");
+    if (!capturing) {
+        ce = cudaEventRecord(w.done, s);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventRecord");
+    }
     return QEC_OK;
 }
 

@@ -1800,6 +1800,9 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
             if (bb != EMPTY64 && 2LL * (long long)(bb >> 32) <= (long long)g.b1) atomicOr(&S.cst1[r], 1);
         }
         T.sync();
+        // pairs within d_1 inside a component; each such pair also names its
+        // two events as each other's partner (xcur is free until the flooder
+        // runs), which is the partner of an accepted two-event cluster
         for (int i = T.tid(); i < npairs; i += T.NT) {
             const int sl = S.plist[i];
             unsigned long long k;
@@ -1807,7 +1810,11 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
             ld_ent(&S.pt[sl], k, pv);
             if (pv > g.d1) continue;
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
-            if (S.comp[a] == S.comp[b]) atomicAdd(&S.cst2[S.comp[a]], 1);
+            if (S.comp[a] == S.comp[b]) {
+                atomicAdd(&S.cst2[S.comp[a]], 1);
+                S.xcur[a] = b;
+                S.xcur[b] = a;
+            }
         }
         T.sync();
         // ---- level-1 clusters: closed forms for isolated pairs / boundary singletons
@@ -1824,10 +1831,9 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
                 S.mate[s] = MATE_BOUNDARY; S.ms[s] = s; S.mo[s] = -1; S.stop[s] = s; S.nroot[s] = -1;
                 t1 = max(t1, bd); ncl1++; nres1++;   // one boundary event at time bd
             } else if (size == 2) {
-                // partner: the other member
-                int other = -1;
-                for (int t2 = 0; t2 < K; t2++)
-                    if (t2 != s && S.comp[t2] == r) { other = t2; break; }
+                // partner: the other member (its pair is the cluster's one pair
+                // within d_1, recorded above)
+                const int other = S.xcur[s];
                 const int d = pair_get(S, C, s, other);
                 const long long ba = (long long)(S.sbnd[s] >> 32), bo = (long long)(S.sbnd[other] >> 32);
                 if (d / 2 <= ba && d / 2 <= bo) {

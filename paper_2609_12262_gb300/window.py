@@ -7,7 +7,8 @@ For each window the library assembles the window syndromes on the device
 (stream bits of its layers XOR the previous window's carry) and decodes them,
 XOR-accumulating the committed observable; the committed edges leaving the
 region flip detectors of the next window (qec_decode_window_batch,
-qec_window_assemble).  This module only sequences those calls.
+qec_window_assemble).  This module only sequences those calls; graph()
+records the whole sequence of one decode into a CUDA graph.
 """
 
 from __future__ import annotations
@@ -73,3 +74,18 @@ class SlidingWindow:
             decode_window_batch([g], rows, obs, carry, status, num_shots=S, stream=stream)
             carry_prev, prev = carry, (a, nl, g)
         return obs, status
+
+    def graph(self, syndromes, num_streams: int):
+        """Record decode(syndromes, num_streams) into a CUDA graph (torch).
+        Returns (graph, obs, status): graph.replay() decodes whatever the
+        `syndromes` tensor holds at that time into the same obs / status
+        tensors.  One uncaptured decode of the same shape runs first (it sizes
+        the library's workspace); replays must not overlap other decodes on
+        the device."""
+        import torch
+        self.decode(syndromes, num_streams)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            obs, status = self.decode(syndromes, num_streams)
+        return g, obs, status
