@@ -325,13 +325,14 @@ bool caps_cover(const SlabCaps &have, const SlabCaps &need) {
 }
 
 // Make sure the workspace of `dev` fits the request; may synchronise the device.
-// A slab layout that already covers the request is kept as it is (no new
-// allocation and no refill), so alternating batch shapes reuse the largest.
+// Unless `exact` (a slab size set through qec_set_tuning), a slab layout that
+// already covers the request is kept as it is (no new allocation and no
+// refill), so alternating batch shapes reuse the largest.
 int ws_ensure(Workspace &w, int dev, SlabCaps caps, long long nwarps, SlabCaps caps2, long long nwarps2,
-              long long nshots) {
+              long long nshots, bool exact) {
     w.device = dev;
-    if (w.slabs && nwarps <= w.nwarps && caps_cover(w.caps, caps)) caps = w.caps;
-    if (w.slabs2 && nwarps2 <= w.nwarps2 && caps_cover(w.caps2, caps2)) caps2 = w.caps2;
+    if (!exact && w.slabs && nwarps <= w.nwarps && caps_cover(w.caps, caps)) caps = w.caps;
+    if (!exact && w.slabs2 && nwarps2 <= w.nwarps2 && caps_cover(w.caps2, caps2)) caps2 = w.caps2;
     const long long sb = qec::slab_bytes_for(caps);
     const long long sb2 = qec::slab_bytes_for(caps2);
     cudaError_t e;
@@ -393,9 +394,11 @@ int ws_ensure(Workspace &w, int dev, SlabCaps caps, long long nwarps, SlabCaps c
 // same slab layouts, nothing left to fill): the condition for decoding inside
 // a stream capture, where nothing may be allocated or synchronised.
 bool ws_fits(const Workspace &w, const SlabCaps &caps, long long nwarps, const SlabCaps &caps2, long long nwarps2,
-             long long nshots) {
+             long long nshots, bool exact) {
     if (!w.done || !w.queue || !w.slabs || !w.slabs2 || w.fill1 || w.fill2) return false;
     if (nwarps > w.nwarps || nwarps2 > w.nwarps2 || nshots > w.overflow_cap) return false;
+    if (exact)
+        return std::memcmp(&w.caps, &caps, sizeof(caps)) == 0 && std::memcmp(&w.caps2, &caps2, sizeof(caps2)) == 0;
     return caps_cover(w.caps, caps) && caps_cover(w.caps2, caps2);
 }
 
@@ -813,10 +816,10 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
     const bool capturing = cap != cudaStreamCaptureStatusNone;
     if (capturing) {
-        if (!ws_fits(w, caps, nwarps, caps2, nwarps2, plain ? 1 : num_shots))
+        if (!ws_fits(w, caps, nwarps, caps2, nwarps2, plain ? 1 : num_shots, tune.kcap > 0))
             return fail(QEC_EINVAL, "stream capture needs a prior uncaptured call of the same shape (workspace not ready)");
     } else {
-        int rc = ws_ensure(w, dev, caps, nwarps, caps2, nwarps2, plain ? 1 : num_shots);
+        int rc = ws_ensure(w, dev, caps, nwarps, caps2, nwarps2, plain ? 1 : num_shots, tune.kcap > 0);
         if (rc != QEC_OK) return rc;
         ce = cudaStreamWaitEvent(s, w.done, 0);
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamWaitEvent");
