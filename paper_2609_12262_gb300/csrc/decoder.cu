@@ -2005,6 +2005,11 @@ __device__ void decode_shot(const BatchArgs &A, const Slab &S, long long shot, T
         A.w_out[shot] = w;
         A.obs_out[shot] = o;
         A.st_out[shot] = status;
+        if (A.done && !retried) {
+            // the results reach the host before the flag that publishes them
+            __threadfence_system();
+            asm volatile("st.release.sys.global.b32 [%0], %1;" :: "l"(A.done + shot), "r"(1) : "memory");
+        }
     }
     T.sync();
 }

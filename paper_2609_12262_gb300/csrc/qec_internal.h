@@ -79,6 +79,10 @@ struct BatchArgs {
     // multi-warp teams: a shot with fewer detection events than this is
     // decoded by the team's first warp alone (0: always by the whole team)
     int team_split;
+    // serving: per-shot completion flags in host memory mapped into the
+    // device (obs_out / w_out / st_out then point there too); set to 1, after
+    // a system-wide fence, once a shot's final results are written, or NULL
+    int *done;
 };
 
 long long slab_bytes_for(const SlabCaps &c);

@@ -7,7 +7,10 @@
 // appends the window to it.  A dispatcher thread launches the FILLING slot as
 // soon as fewer than N-1 slots are INFLIGHT (immediately when the GPU has room,
 // so a lone request is not held back), makes an IDLE slot the new FILLING one,
-// and turns finished slots into results with completion timestamps.  A
+// and hands out each window's result as soon as the kernel has published it:
+// results and per-window completion flags live in pinned host memory mapped
+// into the device, so a small window is not held back by the slowest window
+// of its micro-batch; a slot is reused once all its windows are out.  A
 // micro-batch small enough for one thread block per window is decoded by
 // multi-warp teams (a block of TEAM_BIG warps per window), which cuts the
 // latency of the large windows; larger micro-batches use one warp per window.
@@ -48,15 +51,20 @@ struct Slot {
     int64_t *h_off = nullptr;
     uint64_t *h_rid = nullptr;
     int64_t *h_tsub = nullptr;
+    // results and completion flags: pinned host memory mapped into the device
+    // (h_* host addresses, m_* the device's addresses of the same bytes)
     uint64_t *h_obs = nullptr;
     int64_t *h_w = nullptr;
     int32_t *h_st = nullptr;
+    int32_t *h_done = nullptr;
+    uint64_t *m_obs = nullptr;
+    int64_t *m_w = nullptr;
+    int32_t *m_st = nullptr;
+    int32_t *m_done = nullptr;
+    std::vector<int> pending;   // windows of the in-flight micro-batch not yet handed out
     uint32_t *d_syn = nullptr;
     int32_t *d_gid = nullptr;
     int64_t *d_off = nullptr;
-    uint64_t *d_obs = nullptr;
-    int64_t *d_w = nullptr;
-    int32_t *d_st = nullptr;
     char *slabs = nullptr;
     char *slabs2 = nullptr;
     unsigned long long *queue = nullptr;
@@ -95,8 +103,9 @@ void free_slot(Slot &s) {
     if (s.cs) cudaStreamSynchronize(s.cs);
     cudaFreeHost(s.h_syn); cudaFreeHost(s.h_gid); cudaFreeHost(s.h_off); cudaFreeHost(s.h_rid);
     cudaFreeHost(s.h_tsub); cudaFreeHost(s.h_obs); cudaFreeHost(s.h_w); cudaFreeHost(s.h_st);
-    cudaFree(s.d_syn); cudaFree(s.d_gid); cudaFree(s.d_off); cudaFree(s.d_obs); cudaFree(s.d_w);
-    cudaFree(s.d_st); cudaFree(s.slabs); cudaFree(s.slabs2); cudaFree(s.queue); cudaFree(s.overflow);
+    cudaFreeHost(s.h_done);
+    cudaFree(s.d_syn); cudaFree(s.d_gid); cudaFree(s.d_off);
+    cudaFree(s.slabs); cudaFree(s.slabs2); cudaFree(s.queue); cudaFree(s.overflow);
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.cs) cudaStreamDestroy(s.cs);
     s = Slot();
@@ -111,12 +120,16 @@ bool alloc_slot(qec_stream *st, Slot &s) {
               cudaHostAlloc(&s.h_off, R * 8, cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(&s.h_rid, R * 8, cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc(&s.h_tsub, R * 8, cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc(&s.h_obs, R * 8, cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc(&s.h_w, R * 8, cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc(&s.h_st, R * 4, cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc(&s.h_obs, R * 8, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&s.h_w, R * 8, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&s.h_st, R * 4, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostAlloc(&s.h_done, R * 4, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&s.m_obs, s.h_obs, 0) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&s.m_w, s.h_w, 0) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&s.m_st, s.h_st, 0) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&s.m_done, s.h_done, 0) == cudaSuccess &&
               cudaMalloc(&s.d_syn, W * 4) == cudaSuccess && cudaMalloc(&s.d_gid, R * 4) == cudaSuccess &&
-              cudaMalloc(&s.d_off, R * 8) == cudaSuccess && cudaMalloc(&s.d_obs, R * 8) == cudaSuccess &&
-              cudaMalloc(&s.d_w, R * 8) == cudaSuccess && cudaMalloc(&s.d_st, R * 4) == cudaSuccess &&
+              cudaMalloc(&s.d_off, R * 8) == cudaSuccess &&
               cudaMalloc(&s.slabs, (size_t)(st->sb * st->nwarps)) == cudaSuccess &&
               cudaMalloc(&s.slabs2, (size_t)(st->sb2 * st->nwarps2)) == cudaSuccess &&
               cudaMalloc(&s.queue, 4 * sizeof(unsigned long long)) == cudaSuccess &&
@@ -130,6 +143,12 @@ bool alloc_slot(qec_stream *st, Slot &s) {
 // Enqueue one micro-batch on its slot's stream (the slot is owned by the dispatcher).
 cudaError_t launch_slot(qec_stream *st, Slot &s) {
     cudaError_t e;
+    // completion flags cleared before the launch (the launch orders these host
+    // writes before the kernel's)
+    std::memset(s.h_done, 0, (size_t)s.n * sizeof(int32_t));
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    s.pending.resize((size_t)s.n);
+    for (int k = 0; k < s.n; k++) s.pending[(size_t)k] = k;
     if ((e = cudaMemcpyAsync(s.d_syn, s.h_syn, (size_t)s.words * 4, cudaMemcpyHostToDevice, s.cs))) return e;
     if ((e = cudaMemcpyAsync(s.d_gid, s.h_gid, (size_t)s.n * 4, cudaMemcpyHostToDevice, s.cs))) return e;
     if ((e = cudaMemcpyAsync(s.d_off, s.h_off, (size_t)s.n * 8, cudaMemcpyHostToDevice, s.cs))) return e;
@@ -147,9 +166,10 @@ cudaError_t launch_slot(qec_stream *st, Slot &s) {
     a.graph_of_shot = s.d_gid;
     a.syn_off = reinterpret_cast<const long long *>(s.d_off);
     a.syn = s.d_syn;
-    a.obs_out = reinterpret_cast<unsigned long long *>(s.d_obs);
-    a.w_out = reinterpret_cast<long long *>(s.d_w);
-    a.st_out = s.d_st;
+    a.obs_out = reinterpret_cast<unsigned long long *>(s.m_obs);
+    a.w_out = reinterpret_cast<long long *>(s.m_w);
+    a.st_out = s.m_st;
+    a.done = s.m_done;
     a.queue = s.queue;
     a.overflow = s.overflow;
     a.single_shot = -1;
@@ -180,9 +200,6 @@ cudaError_t launch_slot(qec_stream *st, Slot &s) {
     a.caps = st->caps2;
     a.pass = 1;
     if ((e = qec::launch_batch(a, st->nwarps2, team > 1 ? 32 * team : 32, s.cs, team))) return e;
-    if ((e = cudaMemcpyAsync(s.h_obs, s.d_obs, (size_t)s.n * 8, cudaMemcpyDeviceToHost, s.cs))) return e;
-    if ((e = cudaMemcpyAsync(s.h_w, s.d_w, (size_t)s.n * 8, cudaMemcpyDeviceToHost, s.cs))) return e;
-    if ((e = cudaMemcpyAsync(s.h_st, s.d_st, (size_t)s.n * 4, cudaMemcpyDeviceToHost, s.cs))) return e;
     return cudaEventRecord(s.ev, s.cs);
 }
 
@@ -191,33 +208,47 @@ void dispatcher(qec_stream *st) {
     std::vector<qec_result> out;
     while (!st->stop.load(std::memory_order_relaxed)) {
         bool busy = false;
-        // completions: in-flight slots belong to this thread; query outside the lock
+        // completions: in-flight slots belong to this thread.  Every window
+        // whose flag is set is handed out at once; the slot is reused when the
+        // kernel has finished and every window is out (after a failed launch
+        // the remaining windows end with QEC_SHOT_INTERNAL).
         int inflight = 0;
         for (int i = 0; i < st->nslots; i++) {
             Slot &s = st->slots[i];
             if (s.state != INFLIGHT) continue;
             const cudaError_t q = cudaEventQuery(s.ev);
-            if (q == cudaErrorNotReady) { inflight++; continue; }
+            const bool finished = q != cudaErrorNotReady;
             const int64_t t = mono_ns();
             out.clear();
-            for (int k = 0; k < s.n; k++) {
+            size_t keep = 0;
+            for (size_t j = 0; j < s.pending.size(); j++) {
+                const int k = s.pending[j];
+                const bool flag = __atomic_load_n(&s.h_done[k], __ATOMIC_ACQUIRE) != 0;
+                if (!flag && !finished) { s.pending[keep++] = k; continue; }
                 qec_result r;
                 r.request_id = s.h_rid[k];
-                r.obs = q == cudaSuccess ? s.h_obs[k] : 0;
-                r.weight = q == cudaSuccess ? s.h_w[k] : 0;
-                r.status = q == cudaSuccess ? s.h_st[k] : QEC_SHOT_INTERNAL;
+                const bool ok = flag || q == cudaSuccess;
+                r.obs = ok ? s.h_obs[k] : 0;
+                r.weight = ok ? s.h_w[k] : 0;
+                r.status = ok ? s.h_st[k] : QEC_SHOT_INTERNAL;
                 r.graph_index = s.h_gid[k];
                 r.t_submit_ns = s.h_tsub[k];
                 r.t_done_ns = t;
                 out.push_back(r);
             }
+            s.pending.resize(keep);
+            const bool recycle = finished && keep == 0;
+            if (!recycle) inflight++;
+            if (out.empty() && !recycle) continue;
             std::lock_guard<std::mutex> lk(st->mu);
-            if (q != cudaSuccess && st->err.empty()) st->err = cudaGetErrorString(q);
+            if (finished && q != cudaSuccess && st->err.empty()) st->err = cudaGetErrorString(q);
             st->done.insert(st->done.end(), out.begin(), out.end());
-            st->admitted -= s.n;
-            s.n = 0;
-            s.words = 0;
-            s.state = IDLE;
+            st->admitted -= (int)out.size();
+            if (recycle) {
+                s.n = 0;
+                s.words = 0;
+                s.state = IDLE;
+            }
             busy = true;
         }
         // launch the filling micro-batch when an in-flight slot is free
