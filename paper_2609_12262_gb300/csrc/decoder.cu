@@ -800,8 +800,10 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
         if (lane == 0) S.ctr[C_TL] = ntl;
     }
     T.sync();
-    const int nt = T.bcast(min(ldr(&S.ctr[C_TL]), C.ec));
-    const int e0 = T.bcast(ldr(&S.ctr[C_ECOUNT]));
+    const unsigned long long ne = T.bcast64(((unsigned long long)(unsigned)min(ldr(&S.ctr[C_TL]), C.ec) << 32) |
+                                            (unsigned)ldr(&S.ctr[C_ECOUNT]));
+    const int nt = (int)(unsigned)(ne >> 32);
+    const int e0 = (int)(unsigned)(ne & 0xffffffffu);
     // explored-entry table at most half full, list room left
     if (e0 + nt > C.ec || (unsigned)(e0 + nt) * 2u > C.hmask) {
         if (T.tid() == 0) set_err(S, ERR_CAP);
@@ -969,9 +971,13 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
             S.mate[A] = MATE_BOUNDARY; S.ms[A] = a; S.mo[A] = -1;
         }
     }
-    rA = T.bcast(rA);
-    rB = T.bcast(rB);
-    T.sync();
+    {
+        // both roots in one broadcast (a block's broadcast is also its barrier)
+        const unsigned long long pr = T.bcast64(((unsigned long long)(unsigned)rA << 32) | (unsigned)rB);
+        rA = (int)(unsigned)(pr >> 32);
+        rB = (int)(unsigned)(pr & 0xffffffffu);
+    }
+    if constexpr (NW == 1) T.sync();
     for (int v = T.tid(); v < nhi; v += T.NT) {
         if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0 && (S.nroot[v] == rA || S.nroot[v] == rB)) {
             S.label[v] = 0; S.tpar[v] = -1; S.nroot[v] = -1;
@@ -1028,10 +1034,16 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
             for (int j = 0; j < m; j++) S.bpar[S.cnode[cb + j]] = N;
         }
     }
-    N = T.bcast(N);
-    L = T.bcast(L);
-    Lroot = T.bcast(Lroot);
-    T.sync();
+    {
+        // N, L and whether L was its tree's root in one broadcast (ids < 2^18)
+        const unsigned hi = L >= 0 ? ((unsigned)L | ((unsigned)Lroot << 30)) : 0xffffffffu;
+        const unsigned long long pk = T.bcast64(((unsigned long long)hi << 32) | (unsigned)N);
+        N = (int)(unsigned)(pk & 0xffffffffu);
+        const unsigned h = (unsigned)(pk >> 32);
+        L = h == 0xffffffffu ? -1 : (int)(h & 0x3fffffffu);
+        Lroot = h == 0xffffffffu ? 0 : (int)((h >> 30) & 1u);
+    }
+    if constexpr (NW == 1) T.sync();
     if (N < 0) return;
     nhi = max(nhi, N + 1);
     for (int v = T.tid(); v < nhi; v += T.NT) {
@@ -1213,7 +1225,11 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             if (tn <= C.tcut) C.ncut++;
             C.tlast = (int)tn;
         }
-        T.sync();
+        // The dual update above writes y and srad only.  In a block, the next
+        // barrier is the one each step below starts with (EXTEND reads the radii
+        // after it; the matcher steps read or write no radius before theirs);
+        // one warp keeps its barrier here.
+        if constexpr (NW == 1) T.sync();
         if (kind == EV_EXTEND) {
             // every growing region that reached its explored radius now
             if (T.tid() == 0) S.ctr[C_WL] = 0;
@@ -1229,7 +1245,11 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             T.sync();
             extend_many(S, C, T.bcast(ldr(&S.ctr[C_WL])), T);
         } else if (kind == EV_IMPLODE) {
-            ev_shatter(S, C, S.stop[lo], T);
+            // the blossom is read by every thread before any thread's shatter
+            // loop rewrites the stop pointers
+            const int B = S.stop[lo];
+            if constexpr (NW > 1) T.sync();
+            ev_shatter(S, C, B, T);
         } else if (kind == EV_BOUNDARY) {
             ev_augment(S, C, S.stop[lo], lo, -1, -1, T, nhi);
         } else {
