@@ -564,18 +564,30 @@ def stream_study(q, args, dev):
         b.record()
         torch.cuda.synchronize()
         ms_whole = a.elapsed_time(b)
-        one = t[:pg.words * 1]
+        one = t[:pg.words * 1].clone()
         dec.decode(one, 1)
         torch.cuda.synchronize()
         a.record()
-        dec.decode(one, 1)
+        obs1, st1 = dec.decode(one, 1)
         b.record()
         torch.cuda.synchronize()
         ms_one = a.elapsed_time(b)
+        ref1 = (obs1.clone(), st1.clone())
+        # the same single stream replayed from one captured CUDA graph
+        cg, go1, gs1 = dec.graph(one, 1)
+        cg.replay()
+        torch.cuda.synchronize()
+        a.record()
+        cg.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ms_one_graph = a.elapsed_time(b)
+        graph_same = bool(torch.equal(go1, ref1[0]) and torch.equal(gs1, ref1[1]))
         row = {"d": d, "rounds": R, "W": 2 * d, "C": d, "p": 0.003, "streams": S, "windows": len(dec.windows),
                "sliding_rounds_per_s": S * R / (ms_sw / 1e3), "sliding_us_per_round": ms_sw * 1e3 / (S * R),
                "whole_history_rounds_per_s": S * R / (ms_whole / 1e3),
                "one_stream_us_per_round": ms_one * 1e3 / R,
+               "one_stream_graph_us_per_round": ms_one_graph * 1e3 / R, "graph_same_result": graph_same,
                "same_observable_as_whole": float((obs == wo).double().mean().item()),
                "sliding_nonzero_status": int(torch.count_nonzero(st).item()),
                "whole_nonzero_status": int(torch.count_nonzero(ws).item())}
