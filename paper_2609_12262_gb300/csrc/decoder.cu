@@ -979,9 +979,16 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
     }
     if constexpr (NW == 1) T.sync();
     for (int v = T.tid(); v < nhi; v += T.NT) {
-        if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0 && (S.nroot[v] == rA || S.nroot[v] == rB)) {
-            S.label[v] = 0; S.tpar[v] = -1; S.nroot[v] = -1;
+        bool hit;
+        if constexpr (NW == 1) {
+            hit = S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0 && (S.nroot[v] == rA || S.nroot[v] == rB);
+        } else {
+            // a block scans many more nodes per event: independent loads first
+            // (one round trip per node; measured slower for one warp)
+            const int al = S.alive[v], bp = S.bpar[v], lb = S.label[v], nr = S.nroot[v];
+            hit = al && bp < 0 && lb != 0 && (nr == rA || nr == rB);
         }
+        if (hit) { S.label[v] = 0; S.tpar[v] = -1; S.nroot[v] = -1; }
     }
     T.sync();
 }
@@ -1047,12 +1054,22 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
     if (N < 0) return;
     nhi = max(nhi, N + 1);
     for (int v = T.tid(); v < nhi; v += T.NT) {
-        if (!S.alive[v] || S.bpar[v] >= 0 || v == N) continue;
-        const int tp = S.tpar[v];
-        if (tp >= 0 && S.bpar[tp] == N) S.tpar[v] = N;
-        const int mt = S.mate[v];
-        if (mt >= 0 && S.bpar[mt] == N) S.mate[v] = N;
-        if (Lroot && S.nroot[v] == L) S.nroot[v] = N;
+        if constexpr (NW == 1) {
+            if (!S.alive[v] || S.bpar[v] >= 0 || v == N) continue;
+            const int tp = S.tpar[v];
+            if (tp >= 0 && S.bpar[tp] == N) S.tpar[v] = N;
+            const int mt = S.mate[v];
+            if (mt >= 0 && S.bpar[mt] == N) S.mate[v] = N;
+            if (Lroot && S.nroot[v] == L) S.nroot[v] = N;
+        } else {
+            // independent loads first, the parents' blossom pointers after
+            const int al = S.alive[v], bp = S.bpar[v], tp = S.tpar[v], mt = S.mate[v], nr = S.nroot[v];
+            if (!al || bp >= 0 || v == N) continue;
+            const int btp = tp >= 0 ? S.bpar[tp] : -1, bmt = mt >= 0 ? S.bpar[mt] : -1;
+            if (btp == N) S.tpar[v] = N;
+            if (bmt == N) S.mate[v] = N;
+            if (Lroot && nr == L) S.nroot[v] = N;
+        }
     }
     for (int s = T.tid(); s < C.K; s += T.NT) {
         const int tp = S.stop[s];
@@ -1197,8 +1214,13 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             best = min(best, ev_key(C.t + gap / r, EV_COLLIDE, a, b));
         }
         for (int v = C.K + T.tid(); v < nhi; v += T.NT) {
-            if (S.alive[v] && S.bpar[v] < 0 && S.label[v] == -1)
-                best = min(best, ev_key(C.t + S.y[v], EV_IMPLODE, S.minleaf[v], 0));
+            if constexpr (NW == 1) {
+                if (S.alive[v] && S.bpar[v] < 0 && S.label[v] == -1)
+                    best = min(best, ev_key(C.t + S.y[v], EV_IMPLODE, S.minleaf[v], 0));
+            } else {
+                const int al = S.alive[v], bp = S.bpar[v], lb = S.label[v], yv = S.y[v], ml = S.minleaf[v];
+                if (al && bp < 0 && lb == -1) best = min(best, ev_key(C.t + yv, EV_IMPLODE, ml, 0));
+            }
         }
         T.reduce_ev(best, flags, inner_leaf_min);
         if (flags & 2) return RUN_INTERNAL;
@@ -1212,8 +1234,14 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         const int dt = (int)(tn - C.t);
         if ((unsigned)dt > inner_leaf_min) return RUN_INTERNAL;
         if (dt > 0) {
-            for (int v = T.tid(); v < nhi; v += T.NT)
-                if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0) S.y[v] += S.label[v] * dt;
+            for (int v = T.tid(); v < nhi; v += T.NT) {
+                if constexpr (NW == 1) {
+                    if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0) S.y[v] += S.label[v] * dt;
+                } else {
+                    const int al = S.alive[v], bp = S.bpar[v], lb = S.label[v];
+                    if (al && bp < 0 && lb != 0) S.y[v] += lb * dt;
+                }
+            }
             for (int s = T.tid(); s < C.K; s += T.NT)
                 if (S.inplay[s]) S.srad[s] += S.label[S.stop[s]] * dt;
         }
