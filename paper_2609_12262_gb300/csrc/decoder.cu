@@ -159,6 +159,16 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
     return v;
 }
 
+// The same with the 32-bit reduction unit: the smallest high word, then the
+// smallest low word among the lanes holding it (faster in a block-wide team,
+// measured slower in the one-warp path).
+__device__ __forceinline__ unsigned long long warp_min64_redux(unsigned long long v) {
+    const unsigned hi = (unsigned)(v >> 32);
+    const unsigned mh = __reduce_min_sync(FULL, hi);
+    const unsigned ml = __reduce_min_sync(FULL, hi == mh ? (unsigned)v : 0xffffffffu);
+    return ((unsigned long long)mh << 32) | ml;
+}
+
 __device__ __forceinline__ long long warp_sum64(long long v) {
 #pragma unroll
     for (int o = WS / 2; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -178,9 +188,12 @@ __device__ __forceinline__ unsigned long long warp_xor64(unsigned long long v) {
 // buffer is reused only after every thread has read it).  Functions kept out
 // of line take their Team by value and end with a barrier after their last
 // team operation, so the caller may go on with its own buffer parity.
+struct __align__(16) TSlot {
+    unsigned long long u;
+    int a, b;
+};
 struct TeamShared {
-    unsigned long long u64[2][32];
-    int i32[2][32][2];
+    TSlot s[2][32];
 };
 
 // Per-thread identity of a team member: a one-warp team needs only the lane
@@ -214,9 +227,9 @@ struct Team : TeamId<NW> {
         if constexpr (NW == 1) {
             return __shfl_sync(FULL, v, 0);
         } else {
-            if (tid() == 0) this->sh->i32[this->ph][0][0] = v;
+            if (tid() == 0) this->sh->s[this->ph][0].a = v;
             __syncthreads();
-            v = this->sh->i32[this->ph][0][0];
+            v = this->sh->s[this->ph][0].a;
             this->ph ^= 1;
             return v;
         }
@@ -225,71 +238,49 @@ struct Team : TeamId<NW> {
         if constexpr (NW == 1) {
             return __shfl_sync(FULL, v, 0);
         } else {
-            if (tid() == 0) this->sh->u64[this->ph][0] = v;
+            if (tid() == 0) this->sh->s[this->ph][0].u = v;
             __syncthreads();
-            v = this->sh->u64[this->ph][0];
+            v = this->sh->s[this->ph][0].u;
             this->ph ^= 1;
             return v;
         }
     }
+    // Cross-warp stage of a block reduction: lane 0 of every warp stores its
+    // warp's value in its slot; after the barrier lane w of every warp reads
+    // slot w (one 16-byte load), and each warp reduces those NW values itself.
+    __device__ __forceinline__ TSlot gather(const TSlot &mine, const TSlot &identity) {
+        if (lane == 0) this->sh->s[this->ph][warp()] = mine;
+        __syncthreads();
+        const TSlot x = lane < NW ? this->sh->s[this->ph][lane] : identity;
+        this->ph ^= 1;
+        return x;
+    }
     __device__ __forceinline__ unsigned long long min64(unsigned long long v) {
-        v = warp_min64(v);
-        if constexpr (NW == 1) {
-            return v;
-        } else {
-            if (lane == 0) this->sh->u64[this->ph][warp()] = v;
-            __syncthreads();
-            unsigned long long r = this->sh->u64[this->ph][0];
-            for (int w = 1; w < NW; w++) { const unsigned long long x = this->sh->u64[this->ph][w]; r = x < r ? x : r; }
-            this->ph ^= 1;
-            return r;
-        }
+        if constexpr (NW == 1) return warp_min64(v);
+        else return warp_min64_redux(gather(TSlot{warp_min64_redux(v), 0, 0}, TSlot{EMPTY64, 0, 0}).u);
     }
     __device__ __forceinline__ long long sum64(long long v) {
         v = warp_sum64(v);
-        if constexpr (NW == 1) {
-            return v;
-        } else {
-            if (lane == 0) this->sh->u64[this->ph][warp()] = (unsigned long long)v;
-            __syncthreads();
-            long long r = 0;
-            for (int w = 0; w < NW; w++) r += (long long)this->sh->u64[this->ph][w];
-            this->ph ^= 1;
-            return r;
-        }
+        if constexpr (NW == 1) return v;
+        else return warp_sum64((long long)gather(TSlot{(unsigned long long)v, 0, 0}, TSlot{0, 0, 0}).u);
     }
     __device__ __forceinline__ unsigned long long xor64(unsigned long long v) {
         v = warp_xor64(v);
-        if constexpr (NW == 1) {
-            return v;
-        } else {
-            if (lane == 0) this->sh->u64[this->ph][warp()] = v;
-            __syncthreads();
-            unsigned long long r = 0;
-            for (int w = 0; w < NW; w++) r ^= this->sh->u64[this->ph][w];
-            this->ph ^= 1;
-            return r;
-        }
+        if constexpr (NW == 1) return v;
+        else return warp_xor64(gather(TSlot{v, 0, 0}, TSlot{0, 0, 0}).u);
     }
     // op: 0 = add, 1 = max, 2 = or
     template <int OP>
+    __device__ __forceinline__ int warp_red32(int v) {
+        if constexpr (OP == 0) return (int)__reduce_add_sync(FULL, (unsigned)v);
+        else if constexpr (OP == 1) return __reduce_max_sync(FULL, v);
+        else return (int)__reduce_or_sync(FULL, (unsigned)v);
+    }
+    template <int OP>
     __device__ __forceinline__ int red32(int v) {
-        if constexpr (OP == 0) v = (int)__reduce_add_sync(FULL, (unsigned)v);
-        else if constexpr (OP == 1) v = __reduce_max_sync(FULL, v);
-        else v = (int)__reduce_or_sync(FULL, (unsigned)v);
-        if constexpr (NW == 1) {
-            return v;
-        } else {
-            if (lane == 0) this->sh->i32[this->ph][warp()][0] = v;
-            __syncthreads();
-            int r = this->sh->i32[this->ph][0][0];
-            for (int w = 1; w < NW; w++) {
-                const int x = this->sh->i32[this->ph][w][0];
-                r = OP == 0 ? r + x : (OP == 1 ? (x > r ? x : r) : (r | x));
-            }
-            this->ph ^= 1;
-            return r;
-        }
+        v = warp_red32<OP>(v);
+        if constexpr (NW == 1) return v;
+        else return warp_red32<OP>(gather(TSlot{0, v, 0}, TSlot{0, OP == 1 ? INT_MIN : 0, 0}).a);
     }
     __device__ __forceinline__ int add(int v) { return red32<0>(v); }
     __device__ __forceinline__ int maxi(int v) { return red32<1>(v); }
@@ -297,27 +288,15 @@ struct Team : TeamId<NW> {
     // The event search's reduction in one barrier: smallest key, OR of flags,
     // smallest m (as unsigned).
     __device__ __forceinline__ void reduce_ev(unsigned long long &key, int &flags, unsigned &m) {
-        key = warp_min64(key);
+        if constexpr (NW == 1) key = warp_min64(key);
+        else key = warp_min64_redux(key);
         flags = (int)__reduce_or_sync(FULL, (unsigned)flags);
         m = __reduce_min_sync(FULL, m);
         if constexpr (NW > 1) {
-            if (lane == 0) {
-                this->sh->u64[this->ph][warp()] = key;
-                this->sh->i32[this->ph][warp()][0] = flags;
-                this->sh->i32[this->ph][warp()][1] = (int)m;
-            }
-            __syncthreads();
-            key = this->sh->u64[this->ph][0];
-            flags = this->sh->i32[this->ph][0][0];
-            m = (unsigned)this->sh->i32[this->ph][0][1];
-            for (int w = 1; w < NW; w++) {
-                const unsigned long long x = this->sh->u64[this->ph][w];
-                key = x < key ? x : key;
-                flags |= this->sh->i32[this->ph][w][0];
-                const unsigned y = (unsigned)this->sh->i32[this->ph][w][1];
-                m = y < m ? y : m;
-            }
-            this->ph ^= 1;
+            const TSlot x = gather(TSlot{key, flags, (int)m}, TSlot{EMPTY64, 0, -1});
+            key = warp_min64_redux(x.u);
+            flags = (int)__reduce_or_sync(FULL, (unsigned)x.a);
+            m = __reduce_min_sync(FULL, (unsigned)x.b);
         }
     }
     // Exclusive prefix sum of v over the team's threads in tid order; `total`
@@ -334,24 +313,32 @@ struct Team : TeamId<NW> {
             total = wtot;
             return incl - v;
         } else {
-            if (lane == 0) this->sh->i32[this->ph][warp()][0] = wtot;
-            __syncthreads();
-            int off = 0, tot = 0;
-            for (int w = 0; w < NW; w++) {
-                const int x = this->sh->i32[this->ph][w][0];
-                if (w < warp()) off += x;
-                tot += x;
-            }
-            this->ph ^= 1;
-            total = tot;
+            // lane w holds warp w's total: the warp's offset and the block total
+            const int x = gather(TSlot{0, wtot, 0}, TSlot{0, 0, 0}).a;
+            const int off = (int)__reduce_add_sync(FULL, (unsigned)(lane < warp() ? x : 0));
+            total = (int)__reduce_add_sync(FULL, (unsigned)x);
             return off + incl - v;
         }
     }
 };
 
+// Per-source state read together by the event search, the dual update and
+// the EXTEND scan: one 16-byte record (a single vector load).
+//   stop: top-level matcher node containing the source; srad: Rad(s);
+//   sR: explored radius (-1: never explored); inplay: part of the current run;
+//   sexh: ball exhausted (no vertex left to explore).
+struct __align__(16) SRec {
+    int stop, srad, sR;
+    unsigned char inplay, sexh, pad0, pad1;
+};
+__device__ __forceinline__ int4 ld_src(const SRec *p) { return *reinterpret_cast<const int4 *>(p); }
+__device__ __forceinline__ int rec_inplay(const int4 &r) { return r.w & 0xff; }
+__device__ __forceinline__ int rec_sexh(const int4 &r) { return (r.w >> 8) & 0xff; }
+
 struct Slab {
     // per detection event (source)
-    int *svtx, *srad, *stop, *sR, *sbeg, *scnt, *sexh, *inplay, *comp, *cst0, *cst1, *cst2;
+    SRec *src;
+    int *svtx, *sbeg, *scnt, *comp, *cst0, *cst1, *cst2;
     unsigned long long *sbnd;
     // explored entries (open addressing, keyed by vertex and source); `ent`
     // holds the table slots of every source's bands (band lists)
@@ -381,9 +368,9 @@ __host__ __device__ inline T *bump(char *&p, long long n) {
 
 __host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &S) {
     char *p = base;
-    S.svtx = bump<int>(p, c.kc); S.srad = bump<int>(p, c.kc); S.stop = bump<int>(p, c.kc);
-    S.sR = bump<int>(p, c.kc); S.sbeg = bump<int>(p, c.kc); S.scnt = bump<int>(p, c.kc);
-    S.sexh = bump<int>(p, c.kc); S.inplay = bump<int>(p, c.kc); S.comp = bump<int>(p, c.kc);
+    S.src = bump<SRec>(p, c.kc);
+    S.svtx = bump<int>(p, c.kc); S.sbeg = bump<int>(p, c.kc); S.scnt = bump<int>(p, c.kc);
+    S.comp = bump<int>(p, c.kc);
     S.cst0 = bump<int>(p, c.kc); S.cst1 = bump<int>(p, c.kc); S.cst2 = bump<int>(p, c.kc);
     S.sbnd = bump<unsigned long long>(p, c.kc);
     S.ht = bump<HEnt>(p, c.hc);
@@ -587,11 +574,11 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
     const int r3 = 3 * g.wmin;
     for (int i = T.tid(); i < nx; i += T.NT) {
         const int s = S.xsrc[i];
-        if (S.sR[s] < 0 && S.xR[i] < r3) {
+        if (S.src[s].sR < 0 && S.xR[i] < r3) {
             S.xcur[atomicAdd(&S.ctr[C_FRESH], 1)] = i;
             continue;
         }
-        if (S.sR[s] < 0) {
+        if (S.src[s].sR < 0) {
             unsigned hs;
             const int r = ht_upsert(S, C, S.svtx[s], s, 0, hs);
             if (r < 0) continue;
@@ -788,10 +775,18 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
             }
         }
         T.sync();
-        if constexpr (NW > 1) nwl = ldr(wctr);
-        const int err = ldr(&S.ctr[C_ERR]);
-        bool stop = nwl == 0 || err;
-        if constexpr (NW > 1) stop = T.any(stop);
+        bool stop;
+        if constexpr (NW == 1) {
+            const int err = ldr(&S.ctr[C_ERR]);
+            stop = nwl == 0 || err;
+        } else {
+            // this round's counter is written by no thread until two rounds
+            // on, so every thread reads the same value: a uniform decision
+            // without a reduction (a capacity error ends the rounds once no
+            // insertion succeeds; the caller reads the error word)
+            nwl = ldr(wctr);
+            stop = nwl == 0;
+        }
         if (stop) break;
         nf = min(nwl, C.wc);
         unsigned *t = F; F = Wn; Wn = t;
@@ -824,8 +819,8 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
                 S.xcur[i] = acc;
                 S.sbeg[s] = acc;
                 S.scnt[s] = c;
-                S.sR[s] = S.xR[i];
-                if (c == 0) S.sexh[s] = 1;
+                S.src[s].sR = S.xR[i];
+                if (c == 0) S.src[s].sexh = 1;
                 acc += c;
             }
             S.ctr[C_ECOUNT] = acc;
@@ -845,8 +840,8 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
             S.xcur[i] = acc;
             S.sbeg[s] = acc;
             S.scnt[s] = c;
-            S.sR[s] = S.xR[i];
-            if (c == 0) S.sexh[s] = 1;
+            S.src[s].sR = S.xR[i];
+            if (c == 0) S.src[s].sexh = 1;
             acc += c;
         }
         if (T.tid() == 0) {
@@ -927,7 +922,7 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
 // Grow one source's ball by one band.  Every thread of the team calls.
 template <int NW>
 __device__ void extend_one(const Slab &S, const Shot &C, int s, Team<NW> &T) {
-    if (T.tid() == 0) { S.xsrc[0] = s; S.xR[0] = max(S.sR[s], 0) + C.band; }
+    if (T.tid() == 0) { S.xsrc[0] = s; S.xR[0] = max(S.src[s].sR, 0) + C.band; }
     T.sync();
     extend_many(S, C, 1, T);
 }
@@ -1072,8 +1067,8 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
         }
     }
     for (int s = T.tid(); s < C.K; s += T.NT) {
-        const int tp = S.stop[s];
-        if (tp != N && S.bpar[tp] == N) S.stop[s] = N;
+        const int tp = S.src[s].stop;
+        if (tp != N && S.bpar[tp] == N) S.src[s].stop = N;
     }
     T.sync();
 }
@@ -1082,9 +1077,9 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
 template <int NW>
 __device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> T) {
     for (int s = T.tid(); s < C.K; s += T.NT)
-        if (S.stop[s] == B) {
+        if (S.src[s].stop == B) {
             const int c = child_of(S, B, s);
-            if (c >= 0) S.stop[s] = c; else atomicOr(&S.ctr[C_ERR], ERR_INTERNAL);
+            if (c >= 0) S.src[s].stop = c; else atomicOr(&S.ctr[C_ERR], ERR_INTERNAL);
         }
     T.sync();
     if (T.tid() == 0) {
@@ -1154,8 +1149,8 @@ __device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> 
 
 // Fresh growing root for source s.
 __device__ __forceinline__ void make_root(const Slab &S, int s) {
-    S.alive[s] = 1; S.y[s] = 0; S.srad[s] = 0; S.bpar[s] = -1; S.label[s] = 1;
-    S.tpar[s] = -1; S.mate[s] = MATE_NONE; S.nroot[s] = s; S.stop[s] = s; S.inplay[s] = 1;
+    S.alive[s] = 1; S.y[s] = 0; S.src[s].srad = 0; S.bpar[s] = -1; S.label[s] = 1;
+    S.tpar[s] = -1; S.mate[s] = MATE_NONE; S.nroot[s] = s; S.src[s].stop = s; S.src[s].inplay = 1;
 }
 
 enum { RUN_OK = 0, RUN_NOSOL = 1, RUN_BUDGET = 2, RUN_CAP = 3, RUN_INTERNAL = 4 };
@@ -1176,7 +1171,8 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         unsigned inner_leaf_min = INT_MAX;
         for (int s = T.tid(); s < C.K; s += T.NT) {
             // independent loads first, one dependent load (the label) after
-            const int ip = S.inplay[s], A = S.stop[s], rad = S.srad[s], exh = S.sexh[s], sR = S.sR[s];
+            const int4 r = ld_src(&S.src[s]);
+            const int ip = rec_inplay(r), A = r.x, rad = r.y, exh = rec_sexh(r), sR = r.z;
             const unsigned long long bb = ldr(&S.sbnd[s]);
             if (!ip) continue;
             const int lab = S.label[A];
@@ -1204,8 +1200,9 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             int pv;
             ld_ent(&S.pt[sl], k, pv);
             const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
-            const int ia = S.inplay[a], ib = S.inplay[b], A = S.stop[a], B = S.stop[b];
-            const int ra = S.srad[a], rb = S.srad[b];
+            const int4 qa = ld_src(&S.src[a]), qb = ld_src(&S.src[b]);
+            const int ia = rec_inplay(qa), ib = rec_inplay(qb), A = qa.x, B = qb.x;
+            const int ra = qa.y, rb = qb.y;
             if (!ia || !ib || A == B) continue;
             const int r = S.label[A] + S.label[B];
             if (r <= 0) continue;
@@ -1221,6 +1218,11 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
                 const int al = S.alive[v], bp = S.bpar[v], lb = S.label[v], yv = S.y[v], ml = S.minleaf[v];
                 if (al && bp < 0 && lb == -1) best = min(best, ev_key(C.t + yv, EV_IMPLODE, ml, 0));
             }
+        }
+        // a block resets the EXTEND list counter ahead of the reduction's
+        // barrier (nothing uses it between ball extensions)
+        if constexpr (NW > 1) {
+            if (T.tid() == 0) S.ctr[C_WL] = 0;
         }
         T.reduce_ev(best, flags, inner_leaf_min);
         if (flags & 2) return RUN_INTERNAL;
@@ -1242,8 +1244,10 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
                     if (al && bp < 0 && lb != 0) S.y[v] += lb * dt;
                 }
             }
-            for (int s = T.tid(); s < C.K; s += T.NT)
-                if (S.inplay[s]) S.srad[s] += S.label[S.stop[s]] * dt;
+            for (int s = T.tid(); s < C.K; s += T.NT) {
+                const int4 r = ld_src(&S.src[s]);
+                if (rec_inplay(r)) S.src[s].srad = r.y + S.label[r.x] * dt;
+            }
         }
         C.t = tn;
         if (kind == EV_EXTEND) {
@@ -1259,30 +1263,38 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         // one warp keeps its barrier here.
         if constexpr (NW == 1) T.sync();
         if (kind == EV_EXTEND) {
-            // every growing region that reached its explored radius now
-            if (T.tid() == 0) S.ctr[C_WL] = 0;
-            T.sync();
+            // every growing region that reached its explored radius now.  In a
+            // block the counter is already zero, and each thread reads only the
+            // radii it updated itself (same striding as the dual update)
+            if constexpr (NW == 1) {
+                if (T.tid() == 0) S.ctr[C_WL] = 0;
+                T.sync();
+            }
             for (int s = T.tid(); s < C.K; s += T.NT) {
-                const int rad = S.srad[s];
-                if (S.inplay[s] && !S.sexh[s] && S.label[S.stop[s]] == 1 && S.sR[s] - C.L + 1 - rad <= 0) {
+                const int4 r = ld_src(&S.src[s]);
+                const int rad = r.y;
+                if (rec_inplay(r) && !rec_sexh(r) && S.label[r.x] == 1 && r.z - C.L + 1 - rad <= 0) {
                     const int k = atomicAdd(&S.ctr[C_WL], 1);
                     S.xsrc[k] = s;
-                    S.xR[k] = max(S.sR[s] + C.band, rad + C.L + C.band);
+                    S.xR[k] = max(r.z + C.band, rad + C.L + C.band);
                 }
             }
             T.sync();
-            extend_many(S, C, T.bcast(ldr(&S.ctr[C_WL])), T);
+            // after the barrier the counter stays unchanged until extend_many's
+            // own first barrier: every thread reads the same count
+            if constexpr (NW == 1) extend_many(S, C, T.bcast(ldr(&S.ctr[C_WL])), T);
+            else extend_many(S, C, ldr(&S.ctr[C_WL]), T);
         } else if (kind == EV_IMPLODE) {
             // the blossom is read by every thread before any thread's shatter
             // loop rewrites the stop pointers
-            const int B = S.stop[lo];
+            const int B = S.src[lo].stop;
             if constexpr (NW > 1) T.sync();
             ev_shatter(S, C, B, T);
         } else if (kind == EV_BOUNDARY) {
-            ev_augment(S, C, S.stop[lo], lo, -1, -1, T, nhi);
+            ev_augment(S, C, S.src[lo].stop, lo, -1, -1, T, nhi);
         } else {
             int a = lo, b = hi;
-            int A = S.stop[a], B = S.stop[b];
+            int A = S.src[a].stop, B = S.src[b].stop;
             if (S.label[A] != 1) { int t = A; A = B; B = t; t = a; a = b; b = t; }
             const int lb = S.label[B];
             // 0 blossom, 1 augment, 2 grow, 3 inconsistent
@@ -1317,7 +1329,7 @@ template <int NW>
 __device__ unsigned long long path_obs(const Slab &S, Shot &C, int s, int x, int dx, Team<NW> &T) {
     const DGraph &g = C.g;
     for (int n = 0; n < 1 << 16; n++) {
-        const int more = S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]);
+        const int more = S.src[s].sR < dx && !S.src[s].sexh && !ldr(&S.ctr[C_ERR]);
         if (!T.bcast(more)) break;
         extend_one(S, C, s, T);
     }
@@ -1452,7 +1464,7 @@ __device__ unsigned long long path_commit(const Slab &S, Shot &C, int s, int x, 
                                           unsigned *carry) {
     const DGraph &g = C.g;
     for (int n = 0; n < 1 << 16; n++) {
-        const int more = S.sR[s] < dx && !S.sexh[s] && !ldr(&S.ctr[C_ERR]);
+        const int more = S.src[s].sR < dx && !S.src[s].sexh && !ldr(&S.ctr[C_ERR]);
         if (!T.bcast(more)) break;
         extend_one(S, C, s, T);
     }
@@ -1770,10 +1782,10 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     // sources, leaf nodes, free list
     int nhi = K;
     for (int s = T.tid(); s < K; s += T.NT) {
-        S.srad[s] = 0; S.sR[s] = -1; S.scnt[s] = 0; S.sbeg[s] = 0; S.sexh[s] = 0; S.inplay[s] = 0;
+        S.src[s] = SRec{s, 0, -1, 0, 0, 0, 0}; S.scnt[s] = 0; S.sbeg[s] = 0;
         S.sbnd[s] = EMPTY64;
         S.alive[s] = 0; S.y[s] = 0; S.bpar[s] = -1; S.label[s] = 0; S.tpar[s] = -1;
-        S.mate[s] = MATE_NONE; S.nroot[s] = -1; S.stop[s] = s; S.minleaf[s] = s; S.clen[s] = 0;
+        S.mate[s] = MATE_NONE; S.nroot[s] = -1; S.minleaf[s] = s; S.clen[s] = 0;
     }
     const int nfree = C.nc - K;
     for (int i = T.tid(); i < nfree; i += T.NT) {
@@ -1875,8 +1887,8 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
             if (!ok) continue;
             if (size == 1) {
                 const int bd = (int)(S.sbnd[s] >> 32);
-                S.alive[s] = 1; S.y[s] = bd; S.srad[s] = bd; S.label[s] = 0; S.bpar[s] = -1;
-                S.mate[s] = MATE_BOUNDARY; S.ms[s] = s; S.mo[s] = -1; S.stop[s] = s; S.nroot[s] = -1;
+                S.alive[s] = 1; S.y[s] = bd; S.src[s].srad = bd; S.label[s] = 0; S.bpar[s] = -1;
+                S.mate[s] = MATE_BOUNDARY; S.ms[s] = s; S.mo[s] = -1; S.src[s].stop = s; S.nroot[s] = -1;
                 t1 = max(t1, bd); ncl1++; nres1++;   // one boundary event at time bd
             } else if (size == 2) {
                 // partner: the other member (its pair is the cluster's one pair
@@ -1885,8 +1897,8 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
                 const int d = pair_get(S, C, s, other);
                 const long long ba = (long long)(S.sbnd[s] >> 32), bo = (long long)(S.sbnd[other] >> 32);
                 if (d / 2 <= ba && d / 2 <= bo) {
-                    S.alive[s] = 1; S.y[s] = d / 2; S.srad[s] = d / 2; S.label[s] = 0; S.bpar[s] = -1;
-                    S.mate[s] = other; S.ms[s] = s; S.mo[s] = other; S.stop[s] = s; S.nroot[s] = -1;
+                    S.alive[s] = 1; S.y[s] = d / 2; S.src[s].srad = d / 2; S.label[s] = 0; S.bpar[s] = -1;
+                    S.mate[s] = other; S.ms[s] = s; S.mo[s] = other; S.src[s].stop = s; S.nroot[s] = -1;
                     t1 = max(t1, d / 2); nres1++;   // one collision at time d/2
                     if (s < other) ncl1++;
                 } else {
@@ -1917,7 +1929,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         const bool top = gr >= K;
         if (top) {
             for (int s = T.tid(); s < K; s += T.NT) {
-                if (S.alive[s] || S.stop[s] != s) S.inplay[s] = 1;   // stopped level-1 configuration
+                if (S.alive[s] || S.src[s].stop != s) S.src[s].inplay = 1;   // stopped level-1 configuration
                 else make_root(S, s);
             }
             C.ncut = 0;
@@ -1937,7 +1949,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         }
         if (top) break;
         for (int s = T.tid(); s < K; s += T.NT)
-            if (S.comp[s] == gr) S.inplay[s] = 0;
+            if (S.comp[s] == gr) S.src[s].inplay = 0;
         T.sync();
         e1 = max(e1, C.nm); t1 = max(t1, C.tlast); ntot += C.nm; ncl1++; nres1 += S.cst0[gr];
         gr++;
