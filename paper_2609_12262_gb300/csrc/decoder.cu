@@ -335,6 +335,14 @@ __device__ __forceinline__ int4 ld_src(const SRec *p) { return *reinterpret_cast
 __device__ __forceinline__ int rec_inplay(const int4 &r) { return r.w & 0xff; }
 __device__ __forceinline__ int rec_sexh(const int4 &r) { return (r.w >> 8) & 0xff; }
 
+// Matcher node state read together by the node scans (dual update,
+// implosions, fix-ups): y = the node's own dual, bpar = parent blossom (-1:
+// top level), label = +1 outer / -1 inner / 0 not in a tree, alive.
+struct __align__(16) NRec {
+    int y, bpar, label, alive;
+};
+__device__ __forceinline__ int4 ld_nd(const NRec *p) { return *reinterpret_cast<const int4 *>(p); }
+
 struct Slab {
     // per detection event (source)
     SRec *src;
@@ -352,8 +360,8 @@ struct Slab {
     HEnt *pt;
     int *plist;
     // matcher nodes (leaf s = node s, blossoms above K)
-    int *y, *bpar, *label, *tpar, *tps, *tpo, *mate, *ms, *mo, *nroot, *minleaf, *cbeg, *clen,
-        *alive, *freel, *tmpa, *tmpb, *stk;
+    NRec *nd;
+    int *tpar, *tps, *tpo, *mate, *ms, *mo, *nroot, *minleaf, *cbeg, *clen, *freel, *tmpa, *tmpb, *stk;
     int *cnode, *cs, *co;
     int *ctr;
 };
@@ -381,11 +389,11 @@ __host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &
     S.xidx = bump<int>(p, c.kc);
     S.wcum = bump<int>(p, c.wcap);
     S.pt = bump<HEnt>(p, c.phc); S.plist = bump<int>(p, c.phc);
-    S.y = bump<int>(p, c.nc); S.bpar = bump<int>(p, c.nc); S.label = bump<int>(p, c.nc);
+    S.nd = bump<NRec>(p, c.nc);
     S.tpar = bump<int>(p, c.nc); S.tps = bump<int>(p, c.nc); S.tpo = bump<int>(p, c.nc);
     S.mate = bump<int>(p, c.nc); S.ms = bump<int>(p, c.nc); S.mo = bump<int>(p, c.nc);
     S.nroot = bump<int>(p, c.nc); S.minleaf = bump<int>(p, c.nc); S.cbeg = bump<int>(p, c.nc);
-    S.clen = bump<int>(p, c.nc); S.alive = bump<int>(p, c.nc); S.freel = bump<int>(p, c.nc);
+    S.clen = bump<int>(p, c.nc); S.freel = bump<int>(p, c.nc);
     S.tmpa = bump<int>(p, 2 * c.nc + 64); S.tmpb = bump<int>(p, 2 * c.nc + 64);
     S.stk = bump<int>(p, 4 * c.nc + 64);
     S.cnode = bump<int>(p, c.cc); S.cs = bump<int>(p, c.cc); S.co = bump<int>(p, c.cc);
@@ -932,7 +940,7 @@ __device__ void extend_one(const Slab &S, const Shot &C, int s, Team<NW> &T) {
 // Child of blossom B that contains `leaf` (-1 if B is not an ancestor).
 __device__ __forceinline__ int child_of(const Slab &S, int B, int leaf) {
     int v = leaf;
-    for (int n = 0; n < 1 << 20 && v >= 0 && S.bpar[v] != B; n++) v = S.bpar[v];
+    for (int n = 0; n < 1 << 20 && v >= 0 && S.nd[v].bpar != B; n++) v = S.nd[v].bpar;
     return v;
 }
 
@@ -955,7 +963,7 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
     int rA = 0, rB = -3;
     if (T.tid() == 0) {
         rA = S.nroot[A];
-        const bool bout = B >= 0 && S.label[B] == 1;
+        const bool bout = B >= 0 && S.nd[B].label == 1;
         rB = bout ? S.nroot[B] : -3;
         flip_to_root(S, A);
         if (bout) flip_to_root(S, B);
@@ -976,14 +984,16 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
     for (int v = T.tid(); v < nhi; v += T.NT) {
         bool hit;
         if constexpr (NW == 1) {
-            hit = S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0 && (S.nroot[v] == rA || S.nroot[v] == rB);
+            const int4 q = ld_nd(&S.nd[v]);
+            hit = q.w && q.y < 0 && q.z != 0 && (S.nroot[v] == rA || S.nroot[v] == rB);
         } else {
             // a block scans many more nodes per event: independent loads first
             // (one round trip per node; measured slower for one warp)
-            const int al = S.alive[v], bp = S.bpar[v], lb = S.label[v], nr = S.nroot[v];
+            const int4 q = ld_nd(&S.nd[v]);
+            const int al = q.w, bp = q.y, lb = q.z, nr = S.nroot[v];
             hit = al && bp < 0 && lb != 0 && (nr == rA || nr == rB);
         }
-        if (hit) { S.label[v] = 0; S.tpar[v] = -1; S.nroot[v] = -1; }
+        if (hit) { S.nd[v].label = 0; S.tpar[v] = -1; S.nroot[v] = -1; }
     }
     T.sync();
 }
@@ -991,8 +1001,8 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
 // Event (a): outer A touches frozen B (matched to C).  Thread 0 only.
 __device__ void ev_grow(const Slab &S, int A, int a, int B, int b) {
     const int Cn = S.mate[B];
-    S.label[B] = -1; S.tpar[B] = A; S.tps[B] = b; S.tpo[B] = a; S.nroot[B] = S.nroot[A];
-    S.label[Cn] = 1; S.tpar[Cn] = B; S.tps[Cn] = S.ms[Cn]; S.tpo[Cn] = S.mo[Cn]; S.nroot[Cn] = S.nroot[A];
+    S.nd[B].label = -1; S.tpar[B] = A; S.tps[B] = b; S.tpo[B] = a; S.nroot[B] = S.nroot[A];
+    S.nd[Cn].label = 1; S.tpar[Cn] = B; S.tps[Cn] = S.ms[Cn]; S.tpo[Cn] = S.mo[Cn]; S.nroot[Cn] = S.nroot[A];
 }
 
 // Event (c): outer A, B in one tree form a blossom.  Every thread of the team calls.
@@ -1027,13 +1037,13 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
                 else { S.cs[cb + j] = S.tps[x]; S.co[cb + j] = S.tpo[x]; }
                 ml = min(ml, S.minleaf[x]);
             }
-            S.alive[N] = 1; S.y[N] = 0; S.bpar[N] = -1; S.label[N] = 1;
+            S.nd[N] = NRec{0, -1, 1, 1};
             S.tpar[N] = S.tpar[L]; S.tps[N] = S.tps[L]; S.tpo[N] = S.tpo[L];
             S.mate[N] = S.mate[L]; S.ms[N] = S.ms[L]; S.mo[N] = S.mo[L];
             Lroot = (S.nroot[L] == L);
             S.nroot[N] = Lroot ? N : S.nroot[L];
             S.minleaf[N] = ml; S.cbeg[N] = cb; S.clen[N] = m;
-            for (int j = 0; j < m; j++) S.bpar[S.cnode[cb + j]] = N;
+            for (int j = 0; j < m; j++) S.nd[S.cnode[cb + j]].bpar = N;
         }
     }
     {
@@ -1050,17 +1060,19 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
     nhi = max(nhi, N + 1);
     for (int v = T.tid(); v < nhi; v += T.NT) {
         if constexpr (NW == 1) {
-            if (!S.alive[v] || S.bpar[v] >= 0 || v == N) continue;
+            const int4 q = ld_nd(&S.nd[v]);
+            if (!q.w || q.y >= 0 || v == N) continue;
             const int tp = S.tpar[v];
-            if (tp >= 0 && S.bpar[tp] == N) S.tpar[v] = N;
+            if (tp >= 0 && S.nd[tp].bpar == N) S.tpar[v] = N;
             const int mt = S.mate[v];
-            if (mt >= 0 && S.bpar[mt] == N) S.mate[v] = N;
+            if (mt >= 0 && S.nd[mt].bpar == N) S.mate[v] = N;
             if (Lroot && S.nroot[v] == L) S.nroot[v] = N;
         } else {
             // independent loads first, the parents' blossom pointers after
-            const int al = S.alive[v], bp = S.bpar[v], tp = S.tpar[v], mt = S.mate[v], nr = S.nroot[v];
+            const int4 q = ld_nd(&S.nd[v]);
+            const int al = q.w, bp = q.y, tp = S.tpar[v], mt = S.mate[v], nr = S.nroot[v];
             if (!al || bp >= 0 || v == N) continue;
-            const int btp = tp >= 0 ? S.bpar[tp] : -1, bmt = mt >= 0 ? S.bpar[mt] : -1;
+            const int btp = tp >= 0 ? S.nd[tp].bpar : -1, bmt = mt >= 0 ? S.nd[mt].bpar : -1;
             if (btp == N) S.tpar[v] = N;
             if (bmt == N) S.mate[v] = N;
             if (Lroot && nr == L) S.nroot[v] = N;
@@ -1068,7 +1080,7 @@ __device__ __noinline__ void ev_blossom(const Slab &S, Shot &C, int A, int a, in
     }
     for (int s = T.tid(); s < C.K; s += T.NT) {
         const int tp = S.src[s].stop;
-        if (tp != N && S.bpar[tp] == N) S.src[s].stop = N;
+        if (tp != N && S.nd[tp].bpar == N) S.src[s].stop = N;
     }
     T.sync();
 }
@@ -1096,7 +1108,7 @@ __device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> 
             S.ctr[C_ERR] |= ERR_INTERNAL;
         } else {
             const int rootB = S.nroot[B];
-            for (int j = 0; j < m; j++) S.bpar[S.cnode[cb + j]] = -1;
+            for (int j = 0; j < m; j++) S.nd[S.cnode[cb + j]].bpar = -1;
             const int fwd = ((ic - ip) % m + m) % m;
             const int dir = (fwd % 2 == 0) ? 1 : -1;
             const int L = dir > 0 ? fwd : m - fwd;
@@ -1104,7 +1116,7 @@ __device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> 
             for (int j = 0; j <= L; j++) {
                 const int idx = ((ip + dir * j) % m + m) % m;
                 const int q = S.cnode[cb + idx];
-                S.label[q] = (j % 2 == 0) ? -1 : 1;
+                S.nd[q].label = (j % 2 == 0) ? -1 : 1;
                 S.nroot[q] = rootB;
                 if (j == 0) {
                     S.tpar[q] = P; S.tps[q] = S.tps[B]; S.tpo[q] = S.tpo[B];
@@ -1132,13 +1144,13 @@ __device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> 
                 int lx, lz;
                 if (dir > 0) { lx = S.cs[cb + i1]; lz = S.co[cb + i1]; }
                 else { lx = S.co[cb + i2]; lz = S.cs[cb + i2]; }
-                S.label[x] = 0; S.label[z] = 0;
+                S.nd[x].label = 0; S.nd[z].label = 0;
                 S.tpar[x] = -1; S.tpar[z] = -1;
                 S.nroot[x] = -1; S.nroot[z] = -1;
                 S.mate[x] = z; S.ms[x] = lx; S.mo[x] = lz;
                 S.mate[z] = x; S.ms[z] = lz; S.mo[z] = lx;
             }
-            S.alive[B] = 0; S.tpar[B] = -1; S.mate[B] = MATE_NONE; S.y[B] = 0; S.clen[B] = 0;
+            S.nd[B].alive = 0; S.tpar[B] = -1; S.mate[B] = MATE_NONE; S.nd[B].y = 0; S.clen[B] = 0;
             const int nf = S.ctr[C_NFREE];
             S.freel[nf] = B;
             S.ctr[C_NFREE] = nf + 1;
@@ -1149,7 +1161,7 @@ __device__ __noinline__ void ev_shatter(const Slab &S, Shot &C, int B, Team<NW> 
 
 // Fresh growing root for source s.
 __device__ __forceinline__ void make_root(const Slab &S, int s) {
-    S.alive[s] = 1; S.y[s] = 0; S.src[s].srad = 0; S.bpar[s] = -1; S.label[s] = 1;
+    S.nd[s] = NRec{0, -1, 1, 1}; S.src[s].srad = 0;
     S.tpar[s] = -1; S.mate[s] = MATE_NONE; S.nroot[s] = s; S.src[s].stop = s; S.src[s].inplay = 1;
 }
 
@@ -1175,7 +1187,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             const int ip = rec_inplay(r), A = r.x, rad = r.y, exh = rec_sexh(r), sR = r.z;
             const unsigned long long bb = ldr(&S.sbnd[s]);
             if (!ip) continue;
-            const int lab = S.label[A];
+            const int lab = S.nd[A].label;
             if (lab == 1) {
                 flags |= 1;
                 if (!exh) {
@@ -1190,7 +1202,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
                     else best = min(best, ev_key(C.t + (bd - rad), EV_BOUNDARY, s, ID_MAX));
                 }
             } else if (lab == -1 && A == s) {
-                inner_leaf_min = min(inner_leaf_min, (unsigned)S.y[s]);
+                inner_leaf_min = min(inner_leaf_min, (unsigned)S.nd[s].y);
             }
         }
         const int np = ldr(&S.ctr[C_NPAIRS]);
@@ -1204,7 +1216,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             const int ia = rec_inplay(qa), ib = rec_inplay(qb), A = qa.x, B = qb.x;
             const int ra = qa.y, rb = qb.y;
             if (!ia || !ib || A == B) continue;
-            const int r = S.label[A] + S.label[B];
+            const int r = S.nd[A].label + S.nd[B].label;
             if (r <= 0) continue;
             const int gap = pv - ra - rb;
             if (gap < 0 || gap % r) { flags |= 2; continue; }
@@ -1212,10 +1224,11 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         }
         for (int v = C.K + T.tid(); v < nhi; v += T.NT) {
             if constexpr (NW == 1) {
-                if (S.alive[v] && S.bpar[v] < 0 && S.label[v] == -1)
-                    best = min(best, ev_key(C.t + S.y[v], EV_IMPLODE, S.minleaf[v], 0));
+                const int4 q = ld_nd(&S.nd[v]);
+                if (q.w && q.y < 0 && q.z == -1) best = min(best, ev_key(C.t + q.x, EV_IMPLODE, S.minleaf[v], 0));
             } else {
-                const int al = S.alive[v], bp = S.bpar[v], lb = S.label[v], yv = S.y[v], ml = S.minleaf[v];
+                const int4 q = ld_nd(&S.nd[v]);
+                const int al = q.w, bp = q.y, lb = q.z, yv = q.x, ml = S.minleaf[v];
                 if (al && bp < 0 && lb == -1) best = min(best, ev_key(C.t + yv, EV_IMPLODE, ml, 0));
             }
         }
@@ -1238,15 +1251,16 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         if (dt > 0) {
             for (int v = T.tid(); v < nhi; v += T.NT) {
                 if constexpr (NW == 1) {
-                    if (S.alive[v] && S.bpar[v] < 0 && S.label[v] != 0) S.y[v] += S.label[v] * dt;
+                    const int4 q = ld_nd(&S.nd[v]);
+                    if (q.w && q.y < 0 && q.z != 0) S.nd[v].y = q.x + q.z * dt;
                 } else {
-                    const int al = S.alive[v], bp = S.bpar[v], lb = S.label[v];
-                    if (al && bp < 0 && lb != 0) S.y[v] += lb * dt;
+                    const int4 q = ld_nd(&S.nd[v]);
+                    if (q.w && q.y < 0 && q.z != 0) S.nd[v].y = q.x + q.z * dt;
                 }
             }
             for (int s = T.tid(); s < C.K; s += T.NT) {
                 const int4 r = ld_src(&S.src[s]);
-                if (rec_inplay(r)) S.src[s].srad = r.y + S.label[r.x] * dt;
+                if (rec_inplay(r)) S.src[s].srad = r.y + S.nd[r.x].label * dt;
             }
         }
         C.t = tn;
@@ -1273,7 +1287,7 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             for (int s = T.tid(); s < C.K; s += T.NT) {
                 const int4 r = ld_src(&S.src[s]);
                 const int rad = r.y;
-                if (rec_inplay(r) && !rec_sexh(r) && S.label[r.x] == 1 && r.z - C.L + 1 - rad <= 0) {
+                if (rec_inplay(r) && !rec_sexh(r) && S.nd[r.x].label == 1 && r.z - C.L + 1 - rad <= 0) {
                     const int k = atomicAdd(&S.ctr[C_WL], 1);
                     S.xsrc[k] = s;
                     S.xR[k] = max(r.z + C.band, rad + C.L + C.band);
@@ -1295,8 +1309,8 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         } else {
             int a = lo, b = hi;
             int A = S.src[a].stop, B = S.src[b].stop;
-            if (S.label[A] != 1) { int t = A; A = B; B = t; t = a; a = b; b = t; }
-            const int lb = S.label[B];
+            if (S.nd[A].label != 1) { int t = A; A = B; B = t; t = a; a = b; b = t; }
+            const int lb = S.nd[B].label;
             // 0 blossom, 1 augment, 2 grow, 3 inconsistent
             int act = 3;
             if (lb == 1) act = S.nroot[A] == S.nroot[B] ? 0 : 1;
@@ -1370,7 +1384,7 @@ __device__ __noinline__ void trace(const Slab &S, Shot &C, Team<NW> T, int nhi, 
     T.sync();
     int *stk = S.stk;
     for (int v = T.tid(); v < nhi; v += T.NT) {
-        if (!S.alive[v] || S.bpar[v] >= 0) continue;
+        if (!S.nd[v].alive || S.nd[v].bpar >= 0) continue;
         const int mt = S.mate[v];
         if (mt == MATE_BOUNDARY) {
             const int k = agg_inc(&S.ctr[C_TNP], T.lane);
@@ -1784,14 +1798,14 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
     for (int s = T.tid(); s < K; s += T.NT) {
         S.src[s] = SRec{s, 0, -1, 0, 0, 0, 0}; S.scnt[s] = 0; S.sbeg[s] = 0;
         S.sbnd[s] = EMPTY64;
-        S.alive[s] = 0; S.y[s] = 0; S.bpar[s] = -1; S.label[s] = 0; S.tpar[s] = -1;
+        S.nd[s] = NRec{0, -1, 0, 0}; S.tpar[s] = -1;
         S.mate[s] = MATE_NONE; S.nroot[s] = -1; S.minleaf[s] = s; S.clen[s] = 0;
     }
     const int nfree = C.nc - K;
     for (int i = T.tid(); i < nfree; i += T.NT) {
         const int v = C.nc - 1 - i;   // pop order: K, K+1, ...
         S.freel[i] = v;
-        S.alive[v] = 0; S.clen[v] = 0; S.bpar[v] = -1;
+        S.nd[v] = NRec{0, -1, 0, 0}; S.clen[v] = 0;
     }
     if (T.tid() == 0) { S.ctr[C_ECOUNT] = 0; S.ctr[C_NFREE] = nfree; }
     T.sync();
@@ -1887,7 +1901,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
             if (!ok) continue;
             if (size == 1) {
                 const int bd = (int)(S.sbnd[s] >> 32);
-                S.alive[s] = 1; S.y[s] = bd; S.src[s].srad = bd; S.label[s] = 0; S.bpar[s] = -1;
+                S.nd[s] = NRec{bd, -1, 0, 1}; S.src[s].srad = bd;
                 S.mate[s] = MATE_BOUNDARY; S.ms[s] = s; S.mo[s] = -1; S.src[s].stop = s; S.nroot[s] = -1;
                 t1 = max(t1, bd); ncl1++; nres1++;   // one boundary event at time bd
             } else if (size == 2) {
@@ -1897,7 +1911,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
                 const int d = pair_get(S, C, s, other);
                 const long long ba = (long long)(S.sbnd[s] >> 32), bo = (long long)(S.sbnd[other] >> 32);
                 if (d / 2 <= ba && d / 2 <= bo) {
-                    S.alive[s] = 1; S.y[s] = d / 2; S.src[s].srad = d / 2; S.label[s] = 0; S.bpar[s] = -1;
+                    S.nd[s] = NRec{d / 2, -1, 0, 1}; S.src[s].srad = d / 2;
                     S.mate[s] = other; S.ms[s] = s; S.mo[s] = other; S.src[s].stop = s; S.nroot[s] = -1;
                     t1 = max(t1, d / 2); nres1++;   // one collision at time d/2
                     if (s < other) ncl1++;
@@ -1929,7 +1943,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         const bool top = gr >= K;
         if (top) {
             for (int s = T.tid(); s < K; s += T.NT) {
-                if (S.alive[s] || S.src[s].stop != s) S.src[s].inplay = 1;   // stopped level-1 configuration
+                if (S.nd[s].alive || S.src[s].stop != s) S.src[s].inplay = 1;   // stopped level-1 configuration
                 else make_root(S, s);
             }
             C.ncut = 0;
