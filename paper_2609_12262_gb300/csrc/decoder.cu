@@ -139,6 +139,25 @@ __device__ __forceinline__ bool claim_ent(HEnt *p, unsigned long long key, int d
     return ok == ek && ov == ev;
 }
 
+// Claim an empty pair entry for (key, d) recording pair record idx in the
+// entry's upper word; returns true on success, else the entry found there
+// (key, value | record << 32).
+__device__ __forceinline__ bool claim_pair(HEnt *p, unsigned long long key, int d, int idx,
+                                           unsigned long long &fk, unsigned long long &fv) {
+    const unsigned long long ek = ~0ull, ev = ~0ull;
+    const unsigned long long nv = ((unsigned long long)(unsigned)idx << 32) | (unsigned)d;
+    unsigned long long ok, ov;
+    asm volatile("{\n\t.reg .b128 cmp, swp, old;\n\t"
+                 "mov.b128 cmp, {%2, %3};\n\t"
+                 "mov.b128 swp, {%4, %5};\n\t"
+                 "atom.relaxed.cta.global.cas.b128 old, [%6], cmp, swp;\n\t"
+                 "mov.b128 {%0, %1}, old;\n\t}"
+                 : "=l"(ok), "=l"(ov) : "l"(ek), "l"(ev), "l"(key), "l"(nv), "l"(p) : "memory");
+    fk = ok;
+    fv = ov;
+    return ok == ek && ov == ev;
+}
+
 // Warp-aggregated atomicAdd(ctr, 1) over the currently active lanes.
 __device__ __forceinline__ int agg_inc(int *ctr, int lane) {
     const unsigned m = __activemask();
@@ -343,6 +362,18 @@ struct __align__(16) NRec {
 };
 __device__ __forceinline__ int4 ld_nd(const NRec *p) { return *reinterpret_cast<const int4 *>(p); }
 
+// A pair of events whose balls met, as a block-wide team keeps it: ranks
+// lo < hi, exact distance (equal to the hash entry's value after every
+// barrier), hash slot.  All ones (lo = -1) is an unused record: a record
+// reserved by an insert that lost the race for its slot to the same pair
+// stays so.  A one-warp team lists the pairs' hash slots instead (plist).
+struct __align__(16) PRec {
+    int lo, hi;
+    unsigned val;
+    int slot;
+};
+__device__ __forceinline__ int4 ld_pr(const PRec *p) { return *reinterpret_cast<const int4 *>(p); }
+
 struct Slab {
     // per detection event (source)
     SRec *src;
@@ -356,9 +387,12 @@ struct Slab {
     int *xsrc, *xR, *xcnt, *xcur;         // sources being extended, target radii, band counts
     int *xidx;                            // position of a source in xsrc during an extension
     int *wcum;                            // detection events in syndrome words before word w
-    // pairs: key (lo << 32 | hi), value distance, list of used slots
+    // pairs: key (lo << 32 | hi), value distance; one-warp teams list the
+    // used slots (plist), block-wide teams keep pair records (pr, carved
+    // last) whose index the hash entry's upper word holds
     HEnt *pt;
     int *plist;
+    PRec *pr;
     // matcher nodes (leaf s = node s, blossoms above K)
     NRec *nd;
     int *tpar, *tps, *tpo, *mate, *ms, *mo, *nroot, *minleaf, *cbeg, *clen, *freel, *tmpa, *tmpb, *stk;
@@ -398,6 +432,7 @@ __host__ __device__ inline long long carve(char *base, const SlabCaps &c, Slab &
     S.stk = bump<int>(p, 4 * c.nc + 64);
     S.cnode = bump<int>(p, c.cc); S.cs = bump<int>(p, c.cc); S.co = bump<int>(p, c.cc);
     S.ctr = bump<int>(p, C_TOTAL);
+    S.pr = bump<PRec>(p, (c.phc >> 1) + 1);   // last: the one-warp layout above is unchanged
     return (long long)(p - base) + 16;
 }
 
@@ -481,28 +516,62 @@ __device__ int ht_upsert(const Slab &S, const Shot &C, int v, int s, int d, unsi
     return -1;
 }
 
+// Insert-or-decrease the pair (a, b) with distance d.  REC (block-wide
+// teams): a new pair reserves the next pair record before claiming its slot,
+// and every value written to the hash entry is also applied to the record by
+// the thread that wrote it, so both hold the minimum after the next barrier.
+// Otherwise the claimed slot is appended to the pair list.
+template <bool REC>
 __device__ void pair_upsert(const Slab &S, const Shot &C, int a, int b, int d) {
     int lo = a < b ? a : b, hi = a < b ? b : a;
     const unsigned long long key = ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
     unsigned i = pslot(lo, hi, C.pmask);
-    for (unsigned n = 0; n <= C.pmask; n++) {
-        unsigned long long k;
-        int v;
-        ld_ent(&S.pt[i], k, v);
-        if (k == EMPTY64) {
-            if (claim_ent(&S.pt[i], key, d, k)) {
-                int idx = atomicAdd(&S.ctr[C_NPAIRS], 1);
-                if ((unsigned)idx * 2u > C.pmask) set_err(S, ERR_CAP);
-                else S.plist[idx] = (int)i;
+    if constexpr (REC) {
+        int idx = -1;
+        for (unsigned n = 0; n <= C.pmask; n++) {
+            unsigned long long k, w;
+            asm volatile("ld.relaxed.cta.v2.b64 {%0, %1}, [%2];" : "=l"(k), "=l"(w) : "l"(&S.pt[i]) : "memory");
+            if (k == EMPTY64) {
+                if (idx < 0) {
+                    idx = atomicAdd(&S.ctr[C_NPAIRS], 1);
+                    if ((unsigned)idx * 2u > C.pmask) { set_err(S, ERR_CAP); return; }
+                }
+                if (claim_pair(&S.pt[i], key, d, idx, k, w)) {
+                    S.pr[idx].lo = lo; S.pr[idx].hi = hi; S.pr[idx].slot = (int)i;
+                    atomicMin(&S.pr[idx].val, (unsigned)d);
+                    return;
+                }
+            }
+            if (k == key) {
+                const int v = (int)(unsigned)(w & 0xffffffffu), j = (int)(w >> 32);
+                if (d < v) {
+                    atomicMin(&S.pt[i].val, d);
+                    atomicMin(&S.pr[j].val, (unsigned)d);
+                }
+                return;   // a reserved record stays unused
+            }
+            i = (i + 1) & C.pmask;
+        }
+    } else {
+        for (unsigned n = 0; n <= C.pmask; n++) {
+            unsigned long long k;
+            int v;
+            ld_ent(&S.pt[i], k, v);
+            if (k == EMPTY64) {
+                if (claim_ent(&S.pt[i], key, d, k)) {
+                    int idx = atomicAdd(&S.ctr[C_NPAIRS], 1);
+                    if ((unsigned)idx * 2u > C.pmask) set_err(S, ERR_CAP);
+                    else S.plist[idx] = (int)i;
+                    return;
+                }
+                v = INF32;
+            }
+            if (k == key) {
+                if (d < v) atomicMin(&S.pt[i].val, d);
                 return;
             }
-            v = INF32;
+            i = (i + 1) & C.pmask;
         }
-        if (k == key) {
-            if (d < v) atomicMin(&S.pt[i].val, d);
-            return;
-        }
-        i = (i + 1) & C.pmask;
     }
     set_err(S, ERR_CAP);
 }
@@ -520,6 +589,21 @@ __device__ int pair_get(const Slab &S, const Shot &C, int a, int b) {
         i = (i + 1) & C.pmask;
     }
     return INF32;
+}
+
+// The i-th pair found (ranks a < b, distance pv); false for an unused record.
+template <int NW>
+__device__ __forceinline__ bool pair_at(const Slab &S, int i, int &a, int &b, int &pv) {
+    if constexpr (NW == 1) {
+        unsigned long long k;
+        ld_ent(&S.pt[S.plist[i]], k, pv);
+        a = (int)(k >> 32); b = (int)(unsigned)(k & 0xffffffffu);
+        return true;
+    } else {
+        const int4 pq = ld_pr(&S.pr[i]);
+        a = pq.x; b = pq.y; pv = pq.z;
+        return a >= 0;
+    }
 }
 
 struct SlotV {
@@ -903,7 +987,7 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
                     nprobe = 0;
                     if (yv != S.svtx[s] && is_defect(C, yv)) {
                         const int f = rank_of(S, C, yv);
-                        if (f >= 0 && f != s) pair_upsert(S, C, s, f, dy);
+                        if (f >= 0 && f != s) pair_upsert<(NW > 1)>(S, C, s, f, dy);
                     }
                 }
             }
@@ -917,7 +1001,7 @@ __device__ void extend_many(const Slab &S, const Shot &C, int nx, Team<NW> &T) {
                 } else {
                     if ((int)(k >> 32) == yv) {
                         const int s2 = (int)(unsigned)(k & 0xffffffffu);
-                        if (s2 != s) pair_upsert(S, C, s, s2, dy + v);
+                        if (s2 != s) pair_upsert<(NW > 1)>(S, C, s, s2, dy + v);
                     }
                     pos = (pos + 1) & C.hmask;
                 }
@@ -1207,11 +1291,16 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         }
         const int np = ldr(&S.ctr[C_NPAIRS]);
         for (int i = T.tid(); i < np; i += T.NT) {
-            const int sl = S.plist[i];
-            unsigned long long k;
-            int pv;
-            ld_ent(&S.pt[sl], k, pv);
-            const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
+            int a, b, pv;
+            if constexpr (NW == 1) {
+                unsigned long long k;
+                ld_ent(&S.pt[S.plist[i]], k, pv);
+                a = (int)(k >> 32); b = (int)(unsigned)(k & 0xffffffffu);
+            } else {   // the pair's record: one round trip less
+                const int4 pq = ld_pr(&S.pr[i]);
+                a = pq.x; b = pq.y; pv = pq.z;
+                if (a < 0) continue;
+            }
             const int4 qa = ld_src(&S.src[a]), qb = ld_src(&S.src[b]);
             const int ia = rec_inplay(qa), ib = rec_inplay(qb), A = qa.x, B = qb.x;
             const int ra = qa.y, rb = qb.y;
@@ -1561,13 +1650,24 @@ template <int NW>
 __device__ __noinline__ void release_tables(const Slab &S, const Shot &C, Team<NW> T, bool all) {
     T.sync();
     const HEnt e = HEnt{EMPTY64, -1, -1};
+    const PRec pe = PRec{-1, -1, ~0u, -1};
     if (all) {
         for (unsigned i = T.tid(); i <= C.hmask; i += T.NT) S.ht[i] = e;
         for (unsigned i = T.tid(); i <= C.pmask; i += T.NT) S.pt[i] = e;
+        if constexpr (NW > 1)
+            for (unsigned i = T.tid(); i <= (C.pmask >> 1); i += T.NT) S.pr[i] = pe;
     } else {
         const int ne = ldr(&S.ctr[C_ECOUNT]), np = ldr(&S.ctr[C_NPAIRS]);
         for (int i = T.tid(); i < ne; i += T.NT) S.ht[S.ent[i] & C.hmask] = e;
-        for (int i = T.tid(); i < np; i += T.NT) S.pt[S.plist[i] & C.pmask] = e;
+        if constexpr (NW == 1) {
+            for (int i = T.tid(); i < np; i += T.NT) S.pt[S.plist[i] & C.pmask] = e;
+        } else {
+            for (int i = T.tid(); i < np; i += T.NT) {
+                const int sl = S.pr[i].slot;
+                if (sl >= 0) S.pt[sl & C.pmask] = e;
+                S.pr[i] = pe;
+            }
+        }
     }
     T.sync();
 }
@@ -1632,6 +1732,7 @@ constexpr int LB_CAP = 64;   // vertices one lane holds while exploring one even
 // tables): records every other event within Rb through pair_upsert (from the
 // lower-ranked end only) and the canonical boundary candidate of s.  Returns
 // the number of vertices settled, or -1 if more than LB_CAP lie within Rb.
+template <bool REC>
 __device__ __noinline__ int local_ball(const Slab &S, const Shot &C, int s, int Rb) {
     const DGraph &g = C.g;
     int vv[LB_CAP], dd[LB_CAP];
@@ -1652,7 +1753,7 @@ __device__ __noinline__ int local_ball(const Slab &S, const Shot &C, int s, int 
         const int x = vv[bi], dx = bd;
         if (x != src && is_defect(C, x)) {
             const int f = rank_of(S, C, x);
-            if (f > s) pair_upsert(S, C, s, f, dx);
+            if (f > s) pair_upsert<REC>(S, C, s, f, dx);
         }
         const int r0 = __ldg(g.row + x), r1 = __ldg(g.row + x + 1);
         for (int j = r0; j < r1; j++) {
@@ -1730,7 +1831,7 @@ __device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, c
             if (a.w > Rb) continue;
             if (is_defect(C, a.nbr)) {
                 const int f = rank_of(S, C, a.nbr);
-                if (f > os) pair_upsert(S, C, os, f, a.w);
+                if (f > os) pair_upsert<(NW > 1)>(S, C, os, f, a.w);
             }
             unsigned long long bbest = EMPTY64;
             const int q0 = __ldg(g.row + a.nbr), q1 = __ldg(g.row + a.nbr + 1);
@@ -1744,7 +1845,7 @@ __device__ __noinline__ void level1_2hop(const Slab &S, const Shot &C, int Rb, c
                 }
                 if (nd > Rb || b.nbr == osrc || !is_defect(C, b.nbr)) continue;
                 const int f = rank_of(S, C, b.nbr);
-                if (f > os) pair_upsert(S, C, os, f, nd);
+                if (f > os) pair_upsert<(NW > 1)>(S, C, os, f, nd);
             }
             if (bbest != EMPTY64) atomicMin(&S.sbnd[os], bbest);
         }
@@ -1824,7 +1925,7 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
             level1_2hop(S, C, g.b1, T);
         } else {
             for (int s = T.tid(); s < K; s += T.NT) {
-                const int r = local_ball(S, C, s, g.b1);
+                const int r = local_ball<(NW > 1)>(S, C, s, g.b1);
                 if (r < 0) { S.cst0[s] = 1; any_big = true; } else S.cst0[s] = 0;
             }
         }
@@ -1850,12 +1951,8 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         for (int round = 0; round <= K; round++) {
             bool changed = false;
             for (int i = T.tid(); i < npairs; i += T.NT) {
-                const int sl = S.plist[i];
-                unsigned long long k;
-                int pv;
-                ld_ent(&S.pt[sl], k, pv);
-                if (pv > g.b1) continue;
-                const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
+                int a, b, pv;
+                if (!pair_at<NW>(S, i, a, b, pv) || pv > g.b1) continue;
                 const int la = ldr(&S.comp[a]), lb = ldr(&S.comp[b]);
                 if (la != lb) {
                     const int m = min(la, lb);
@@ -1878,12 +1975,8 @@ __device__ int decode_attempt_body(const BatchArgs &A, const Slab &S, const DGra
         // two events as each other's partner (xcur is free until the flooder
         // runs), which is the partner of an accepted two-event cluster
         for (int i = T.tid(); i < npairs; i += T.NT) {
-            const int sl = S.plist[i];
-            unsigned long long k;
-            int pv;
-            ld_ent(&S.pt[sl], k, pv);
-            if (pv > g.d1) continue;
-            const int a = (int)(k >> 32), b = (int)(unsigned)(k & 0xffffffffu);
+            int a, b, pv;
+            if (!pair_at<NW>(S, i, a, b, pv) || pv > g.d1) continue;
             if (S.comp[a] == S.comp[b]) {
                 atomicAdd(&S.cst2[S.comp[a]], 1);
                 S.xcur[a] = b;
