@@ -1045,10 +1045,9 @@ __device__ void flip_to_root(const Slab &S, int A) {
 template <int NW>
 __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, int B, int b, Team<NW> T, int nhi) {
     int rA = 0, rB = -3;
-    if (T.tid() == 0) {
-        rA = S.nroot[A];
-        const bool bout = B >= 0 && S.nd[B].label == 1;
-        rB = bout ? S.nroot[B] : -3;
+    bool bout = false;
+    // flip the matches along both tree paths and match A with B (thread 0)
+    auto rematch = [&]() {
         flip_to_root(S, A);
         if (bout) flip_to_root(S, B);
         if (B >= 0) {
@@ -1057,6 +1056,12 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
         } else {
             S.mate[A] = MATE_BOUNDARY; S.ms[A] = a; S.mo[A] = -1;
         }
+    };
+    if (T.tid() == 0) {
+        rA = S.nroot[A];
+        bout = B >= 0 && S.nd[B].label == 1;
+        rB = bout ? S.nroot[B] : -3;
+        if constexpr (NW == 1) rematch();
     }
     {
         // both roots in one broadcast (a block's broadcast is also its barrier)
@@ -1064,20 +1069,26 @@ __device__ __noinline__ void ev_augment(const Slab &S, Shot &C, int A, int a, in
         rA = (int)(unsigned)(pr >> 32);
         rB = (int)(unsigned)(pr & 0xffffffffu);
     }
-    if constexpr (NW == 1) T.sync();
-    for (int v = T.tid(); v < nhi; v += T.NT) {
-        bool hit;
-        if constexpr (NW == 1) {
+    if constexpr (NW == 1) {
+        T.sync();
+        for (int v = T.tid(); v < nhi; v += T.NT) {
             const int4 q = ld_nd(&S.nd[v]);
-            hit = q.w && q.y < 0 && q.z != 0 && (S.nroot[v] == rA || S.nroot[v] == rB);
-        } else {
-            // a block scans many more nodes per event: independent loads first
-            // (one round trip per node; measured slower for one warp)
-            const int4 q = ld_nd(&S.nd[v]);
-            const int al = q.w, bp = q.y, lb = q.z, nr = S.nroot[v];
-            hit = al && bp < 0 && lb != 0 && (nr == rA || nr == rB);
+            if (q.w && q.y < 0 && q.z != 0 && (S.nroot[v] == rA || S.nroot[v] == rB)) {
+                S.nd[v].label = 0; S.tpar[v] = -1; S.nroot[v] = -1;
+            }
         }
-        if (hit) { S.nd[v].label = 0; S.tpar[v] = -1; S.nroot[v] = -1; }
+    } else {
+        // The two trees' nodes leave them (label and root cleared; a node's
+        // tree parent is only read while it is in a tree, and is set again when
+        // it joins one), while thread 0 rewrites the matches along the tree
+        // paths, which reads tree parents and writes only mates: the two
+        // overlap.  Independent loads first (one round trip per node).
+        for (int v = T.tid(); v < nhi; v += T.NT) {
+            const int4 q = ld_nd(&S.nd[v]);
+            const int nr = S.nroot[v];
+            if (q.w && q.y < 0 && q.z != 0 && (nr == rA || nr == rB)) { S.nd[v].label = 0; S.nroot[v] = -1; }
+        }
+        if (T.tid() == 0) rematch();
     }
     T.sync();
 }
@@ -1265,12 +1276,12 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
         unsigned long long best = EMPTY64;
         int flags = 0;   // bit 0: a growing region exists, bit 1: inconsistent state
         unsigned inner_leaf_min = INT_MAX;
-        for (int s = T.tid(); s < C.K; s += T.NT) {
+        auto src_item = [&](int s) {
             // independent loads first, one dependent load (the label) after
             const int4 r = ld_src(&S.src[s]);
             const int ip = rec_inplay(r), A = r.x, rad = r.y, exh = rec_sexh(r), sR = r.z;
             const unsigned long long bb = ldr(&S.sbnd[s]);
-            if (!ip) continue;
+            if (!ip) return;
             const int lab = S.nd[A].label;
             if (lab == 1) {
                 flags |= 1;
@@ -1288,9 +1299,8 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             } else if (lab == -1 && A == s) {
                 inner_leaf_min = min(inner_leaf_min, (unsigned)S.nd[s].y);
             }
-        }
-        const int np = ldr(&S.ctr[C_NPAIRS]);
-        for (int i = T.tid(); i < np; i += T.NT) {
+        };
+        auto pair_item = [&](int i) {
             int a, b, pv;
             if constexpr (NW == 1) {
                 unsigned long long k;
@@ -1299,26 +1309,40 @@ __device__ int run_matcher(const Slab &S, Shot &C, Team<NW> &T, int &nhi) {
             } else {   // the pair's record: one round trip less
                 const int4 pq = ld_pr(&S.pr[i]);
                 a = pq.x; b = pq.y; pv = pq.z;
-                if (a < 0) continue;
+                if (a < 0) return;
             }
             const int4 qa = ld_src(&S.src[a]), qb = ld_src(&S.src[b]);
             const int ia = rec_inplay(qa), ib = rec_inplay(qb), A = qa.x, B = qb.x;
             const int ra = qa.y, rb = qb.y;
-            if (!ia || !ib || A == B) continue;
+            if (!ia || !ib || A == B) return;
             const int r = S.nd[A].label + S.nd[B].label;
-            if (r <= 0) continue;
+            if (r <= 0) return;
             const int gap = pv - ra - rb;
-            if (gap < 0 || gap % r) { flags |= 2; continue; }
+            if (gap < 0 || gap % r) { flags |= 2; return; }
             best = min(best, ev_key(C.t + gap / r, EV_COLLIDE, a, b));
-        }
-        for (int v = C.K + T.tid(); v < nhi; v += T.NT) {
+        };
+        auto node_item = [&](int v) {
+            const int4 q = ld_nd(&S.nd[v]);
             if constexpr (NW == 1) {
-                const int4 q = ld_nd(&S.nd[v]);
                 if (q.w && q.y < 0 && q.z == -1) best = min(best, ev_key(C.t + q.x, EV_IMPLODE, S.minleaf[v], 0));
             } else {
-                const int4 q = ld_nd(&S.nd[v]);
-                const int al = q.w, bp = q.y, lb = q.z, yv = q.x, ml = S.minleaf[v];
-                if (al && bp < 0 && lb == -1) best = min(best, ev_key(C.t + yv, EV_IMPLODE, ml, 0));
+                const int ml = S.minleaf[v];
+                if (q.w && q.y < 0 && q.z == -1) best = min(best, ev_key(C.t + q.x, EV_IMPLODE, ml, 0));
+            }
+        };
+        const int np = ldr(&S.ctr[C_NPAIRS]);
+        if constexpr (NW == 1) {
+            for (int s = T.tid(); s < C.K; s += T.NT) src_item(s);
+            for (int i = T.tid(); i < np; i += T.NT) pair_item(i);
+            for (int v = C.K + T.tid(); v < nhi; v += T.NT) node_item(v);
+        } else {
+            // one strided pass over sources, pairs and blossoms together, so
+            // every thread of the block gets the same number of items
+            const int n1 = C.K, n2 = C.K + np, n3 = np + nhi;
+            for (int j = T.tid(); j < n3; j += T.NT) {
+                if (j < n1) src_item(j);
+                else if (j < n2) pair_item(j - n1);
+                else node_item(j - np);
             }
         }
         // a block resets the EXTEND list counter ahead of the reduction's
