@@ -313,9 +313,13 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
  * 16 = one thread block of that many warps per shot (every step of the shot
  * spread over the block: the latency path for large windows).  Automatic, for
  * a batch whose largest graph has at least team_min_detectors detectors: 16
- * when the batch has at most one shot per SM, 4 while it has fewer shots than
- * half the one-warp teams the GPU holds at once, else 1 (and always 1
- * for smaller graphs).  Results do not depend on it. */
+ * when the batch has at most one shot per SM, 4 when the largest graph has at
+ * least 32,768 detectors or the batch has fewer shots than half the one-warp
+ * teams the GPU holds at once, else 1 (and always 1 for smaller graphs).
+ * Results do not depend on it.  Shots with more detection events than kcap
+ * go to a second pass with one team per SM: for windows that large (over
+ * 1,024 events with the default kcap) raise kcap to keep them in the main
+ * pass. */
 typedef struct {
     int32_t warps_per_block;   /* 1 .. 32 */
     int32_t blocks_per_sm;     /* 1 .. 64 */

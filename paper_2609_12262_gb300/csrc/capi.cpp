@@ -782,16 +782,21 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     // team size: warps that decode one shot together (the sliding-window
     // kernel is compiled for one warp and for TEAM_BIG warps per shot)
     // automatic choice for a large graph: one 16-warp block per shot when the
-    // batch has at most one shot per SM, 4-warp blocks while it has fewer
-    // shots than half the resident one-warp teams (a shot per warp
-    // would leave most of the GPU idle), else one warp per shot
+    // batch has at most one shot per SM; 4-warp blocks for graphs of at least
+    // kTeamMidDetectors detectors (windows of d >= 41: on a GB300 4-warp blocks
+    // decoded 2,000 - 4,000 d = 41 windows at p = 0.003 1.6 - 1.9x faster than
+    // one warp per window, 3,000 d = 51 windows 2.0x, and lost 18 % only at
+    // d = 41, p = 0.001) or while the batch has fewer shots than half the
+    // resident one-warp teams (a shot per warp would leave most of the GPU
+    // idle); else one warp per shot
+    constexpr int kTeamMidDetectors = 32768;
     int team = tune.team_warps;
     if (team <= 0) {
         team = 1;
         if (!plain && nmax >= tune.team_min_detectors) {
             const long long resident = (long long)sms * bps * wpb;
             if (num_shots <= sms) team = qec::TEAM_BIG;
-            else if (num_shots * 2 < resident) team = qec::TEAM_MID;
+            else if (nmax >= kTeamMidDetectors || num_shots * 2 < resident) team = qec::TEAM_MID;
         }
     }
     if (window && team == qec::TEAM_MID) team = 1;

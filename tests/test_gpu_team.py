@@ -184,3 +184,32 @@ def test_team_split_threshold(qd):
     for split in (1, 40, 100000):
         gpu = with_team(qd, 16, gpu_decode, qd, gg, (syn, offs), gid=gid, split=split)
         assert_same(gpu, ref, "split %d" % split)
+
+
+def test_automatic_team_on_a_batch_of_large_windows(qd):
+    """More d = 41 windows than SMs: the automatic choice (4-warp blocks for
+    graphs of at least 32,768 detectors) gives the same results as one warp and
+    as 16 warps per window, and the oracle's on a sample."""
+    import torch
+    pg = rotated_surface_code(41, 41, 0.003)
+    g = qd.Graph.from_phys(pg)
+    n = 200
+    syn, _ = sample_shots(pg, n, 4141)
+    K = np.unpackbits(syn.view(np.uint8), axis=1).sum(axis=1)
+    t = torch.from_numpy(syn.view(np.int32).reshape(-1)).cuda()
+    qd.set_tuning(kcap=int(K.max()) + 64)
+    try:
+        outs = {}
+        for team in (-1, 1, 16):
+            qd.set_tuning(team_warps=team)
+            o, w, st = qd.decode_batch([g], t, num_shots=n)
+            torch.cuda.synchronize()
+            outs[team] = (w.cpu().numpy(), qd.to_uint64(o), st.cpu().numpy())
+    finally:
+        qd.set_tuning(team_warps=-1, kcap=-1)
+    for team in (1, 16):
+        for a, b in zip(outs[-1], outs[team]):
+            assert np.array_equal(a, b), team
+    assert not outs[-1][2].any()
+    ref = oracle_decode([pg], np.zeros(2, np.int32), list(syn[:2]), chunk=1)
+    assert_same(tuple(x[:2] for x in outs[-1]), ref, "d41 automatic team, first windows")
