@@ -849,6 +849,15 @@ def scaling_line(q, args, dev):
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
+        # the team size chosen by the autotuner for this batch (results equal
+        # across candidates), against the automatic rule above
+        tuned_team, team_ms = autotune.tune_team([g], t, num_shots=n, reps=1)
+        ref_auto = tuple(x.cpu() for x in res)
+        q.decode_batch([g], t, num_shots=n, out=res)
+        torch.cuda.synchronize()
+        assert all(torch.equal(x, y.cpu()) for x, y in zip(ref_auto, res))
+        tuned_ms = min(m for m, tm in team_ms if tm == tuned_team)
+        q.set_tuning(team_warps=-1)
         lat = {}
         one = []
         for team in (16, 1):
@@ -869,6 +878,9 @@ def scaling_line(q, args, dev):
         out["d%d" % d] = {"d": d, "rounds": d, "p": 0.003, "windows": n, "mean_events": float(K.mean()),
                           "batched_windows_per_s": n / (ms / 1e3), "batched_us_per_round": ms * 1e3 / n / d,
                           "batched_team_warps": "automatic",
+                          "tuned_team_warps": tuned_team, "tuned_windows_per_s": n / (tuned_ms / 1e3),
+                          "tuned_us_per_round": tuned_ms * 1e3 / n / d,
+                          "team_ms": {str(tm): m for m, tm in team_ms},
                           "latency_us": lat[16] * 1e3, "latency_us_per_round": lat[16] * 1e3 / d,
                           "latency_team_warps": 16, "one_warp_latency_us": lat[1] * 1e3,
                           "team_speedup": lat[1] / lat[16],

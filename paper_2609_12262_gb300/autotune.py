@@ -8,6 +8,9 @@ observables and statuses as the first one (tuning never changes results), and
 stores the fastest in a JSON cache keyed by GPU name and graph set.
 tune_split() chooses, for single windows decoded by a 16-warp block, the
 detection-event count below which the block's first warp decodes alone.
+tune_team() chooses how many warps decode one shot (1, 4 or 16) for the
+caller's batch: the automatic rule only sees graph sizes and shot counts,
+while the best team size follows the detection events per shot.
 """
 
 from __future__ import annotations
@@ -149,4 +152,42 @@ def tune_split(samples, splits=(1, 24, 48, 64, 96, 128, 192), team: int = 16, re
     totals.sort()
     best = totals[0][1]
     set_tuning(team_split_events=best)
+    return best, totals
+
+
+def tune_team(graphs, syn, graph_of_shot=None, offsets=None, num_shots=None, teams=(1, 4, 16), reps: int = 2):
+    """Choose the team size (warps per shot) for a batch: the batch is decoded
+    with every candidate, the results must agree across candidates, and the
+    fastest is applied and returned with the per-candidate times (ms)."""
+    import torch
+    if num_shots is None:
+        num_shots = int(graph_of_shot.shape[0]) if graph_of_shot is not None else int(syn.numel() // graphs[0].words)
+    dev = syn.device
+    out = (torch.empty(num_shots, dtype=torch.int64, device=dev), torch.empty(num_shots, dtype=torch.int64, device=dev),
+           torch.empty(num_shots, dtype=torch.int32, device=dev))
+    saved = get_tuning()
+    ref = None
+    totals = []
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        for team in teams:
+            set_tuning(team_warps=team)
+            decode_batch(graphs, syn, graph_of_shot, offsets, num_shots=num_shots, out=out)   # warm, sizes the workspace
+            torch.cuda.synchronize()
+            got = tuple(t.cpu().numpy().copy() for t in out)
+            if ref is None:
+                ref = got
+            elif not all(np.array_equal(x, y) for x, y in zip(got, ref)):
+                raise RuntimeError("team size %d changed the decoding result" % team)
+            a.record()
+            for _ in range(reps):
+                decode_batch(graphs, syn, graph_of_shot, offsets, num_shots=num_shots, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            totals.append((a.elapsed_time(b) / reps, team))
+    finally:
+        set_tuning(**{k: _v(v) for k, v in saved.items()})
+    totals.sort()
+    best = totals[0][1]
+    set_tuning(team_warps=best)
     return best, totals

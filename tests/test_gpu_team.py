@@ -213,3 +213,24 @@ def test_automatic_team_on_a_batch_of_large_windows(qd):
     assert not outs[-1][2].any()
     ref = oracle_decode([pg], np.zeros(2, np.int32), list(syn[:2]), chunk=1)
     assert_same(tuple(x[:2] for x in outs[-1]), ref, "d41 automatic team, first windows")
+
+
+def test_team_autotuner_picks_a_size_without_changing_results(qd):
+    """autotune.tune_team decodes the batch with every team size, requires the
+    same results and applies the fastest."""
+    import torch
+    from paper_2609_12262_gb300 import autotune
+    pg = rotated_surface_code(25, 25, 0.003)
+    g = qd.Graph.from_phys(pg)
+    syn, _ = sample_shots(pg, 300, 2525)
+    t = torch.from_numpy(syn.view(np.int32).reshape(-1)).cuda()
+    try:
+        best, totals = autotune.tune_team([g], t, num_shots=300, reps=1)
+        assert best in (1, 4, 16) and sorted(tm for _, tm in totals) == [1, 4, 16]
+        assert qd.get_tuning()["team_warps"] == best
+        o, w, st = qd.decode_batch([g], t, num_shots=300)
+        torch.cuda.synchronize()
+    finally:
+        qd.set_tuning(team_warps=-1)
+    ref = oracle_decode([pg], np.zeros(40, np.int32), list(syn[:40]))
+    assert_same((w.cpu().numpy()[:40], qd.to_uint64(o)[:40], st.cpu().numpy()[:40]), ref, "tuned team, d25")
