@@ -302,7 +302,8 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
  * binding; all have safe defaults).  In qec_set_tuning a positive value sets
  * a knob, zero keeps its current value and a negative value restores the
  * default (warps_per_block 4, blocks_per_sm 0 = as many as fit, band_factor 1,
- * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, max_events 4e6,
+ * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, or to 64 .. 2048 for graphs
+ * of at least 32,768 detectors, max_events 4e6,
  * team_warps 0 = automatic, team_min_detectors 2048, team_split_events 1:
  * every shot of a block goes to the whole block; on a GB300 the autotuner's
  * split search found no threshold faster than that for single windows).
@@ -317,9 +318,8 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
  * least 32,768 detectors or the batch has fewer shots than half the one-warp
  * teams the GPU holds at once, else 1 (and always 1 for smaller graphs).
  * Results do not depend on it.  Shots with more detection events than kcap
- * go to a second pass with one team per SM: for windows that large (over
- * 1,024 events with the default kcap) raise kcap to keep them in the main
- * pass. */
+ * go to a second pass with one team per SM: for windows larger than the
+ * default kcap holds, raise kcap to keep them in the main pass. */
 typedef struct {
     int32_t warps_per_block;   /* 1 .. 32 */
     int32_t blocks_per_sm;     /* 1 .. 64 */

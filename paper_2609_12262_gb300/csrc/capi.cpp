@@ -309,10 +309,18 @@ void ws_free(Workspace &w) {
     w.overflow_cap = 0;
 }
 
+// Graphs this large are decoded by block-wide teams under the automatic team
+// choice (windows of d >= 41).
+constexpr int kTeamMidDetectors = 32768;
+
+// Default detection events per main-pass slab: num_detectors / 16, clamped to
+// 64 .. 1024, or to 64 .. 2048 for graphs of at least kTeamMidDetectors
+// detectors (a d = 51 window at p = 0.003 holds ~1,200 events; past kcap a
+// shot goes to the overflow pass, which has one team per SM).
 int kcap_for(int nmax, const qec_tuning &t) {
     if (t.kcap > 0) return std::min(t.kcap, std::max(1, nmax));
     int k = nmax / 16;
-    k = std::max(64, std::min(1024, k));
+    k = std::max(64, std::min(nmax >= kTeamMidDetectors ? 2048 : 1024, k));
     return std::min(k, std::max(nmax, 1));
 }
 
@@ -771,7 +779,10 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     const int sms = sm_count(dev);
     const int kcap = kcap_for(nmax, tune);
     SlabCaps caps = qec::caps_for_kcap(kcap);
-    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, std::min(nmax, 4 * kcap)), 3);
+    // overflow slabs: four times the events (a default capacity above 1,024
+    // keeps the overflow slabs at 4,096 events, as with a 1,024 main pass)
+    const int kcap2 = (tune.kcap > 0 || kcap <= 1024) ? std::min(nmax, 4 * kcap) : std::min(nmax, 4096);
+    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, kcap2), 3);
     int wmax_words = 0;
     for (int i = 0; i < num_graphs; i++) wmax_words = std::max(wmax_words, graphs[i]->words);
     caps.wcap = std::max(caps.wcap, wmax_words);
@@ -789,7 +800,6 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     // d = 41, p = 0.001) or while the batch has fewer shots than half the
     // resident one-warp teams (a shot per warp would leave most of the GPU
     // idle); else one warp per shot
-    constexpr int kTeamMidDetectors = 32768;
     int team = tune.team_warps;
     if (team <= 0) {
         team = 1;
