@@ -339,7 +339,7 @@ def serving_run(q, args, dev, data, rate, seconds, oracle_n=0):
         sched = t0 + (arr * 1e9).astype(np.int64)
         ids = np.arange(N, dtype=np.uint64)
         got_w = np.zeros(N, np.int64); got_o = np.zeros(N, np.uint64); got_s = np.full(N, -1, np.int32)
-        t_done = np.zeros(N, np.int64)
+        t_done = np.zeros(N, np.int64); t_sub = np.zeros(N, np.int64)
         i, n_done = 0, 0
         deadline = time.monotonic() + 30 + 4 * seconds
         while n_done < N and time.monotonic() < deadline:
@@ -351,6 +351,7 @@ def serving_run(q, args, dev, data, rate, seconds, oracle_n=0):
             if len(r):
                 k = r["request_id"].astype(np.int64)
                 got_w[k] = r["weight"]; got_o[k] = r["obs"]; got_s[k] = r["status"]; t_done[k] = r["t_done_ns"]
+                t_sub[k] = r["t_submit_ns"]
                 n_done += len(r)
     finally:
         import gc
@@ -358,6 +359,10 @@ def serving_run(q, args, dev, data, rate, seconds, oracle_n=0):
         st.close()
     ok = got_s >= 0
     lat_us = (t_done[ok] - sched[ok]) / 1e3
+    # where the latency goes: the host loop's delay in submitting a window
+    # after its scheduled arrival, and submission to result in the library
+    sub_us = (t_sub[ok] - sched[ok]) / 1e3
+    svc_us = (t_done[ok] - t_sub[ok]) / 1e3
     span = (t_done[ok].max() - t0) / 1e9 if ok.any() else float("nan")
     # same windows through the batched path: every served result must agree
     t_syn = torch.from_numpy(syn.view(np.int32)).to(dev)
@@ -384,6 +389,10 @@ def serving_run(q, args, dev, data, rate, seconds, oracle_n=0):
             "sustained": float(ok.sum() / span), "unit": "windows/s",
             "p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
             "p999_us": float(np.percentile(lat_us, 99.9)), "max_us": float(lat_us.max()),
+            "submit_delay_p50_us": float(np.percentile(sub_us, 50)), "submit_delay_p99_us": float(np.percentile(sub_us, 99)),
+            "submit_delay_max_us": float(sub_us.max()),
+            "library_p50_us": float(np.percentile(svc_us, 50)), "library_p99_us": float(np.percentile(svc_us, 99)),
+            "library_max_us": float(svc_us.max()),
             "distances": sds, "p": args.p, "mismatch_vs_batch": mism, "oracle": oracle_check,
             "team_warps": q.get_tuning()["team_warps"] or "auto",
             "latency": "result available on the host minus the scheduled Poisson arrival"}
@@ -403,7 +412,7 @@ def serving_all(q, args, dev):
         else:
             rec = serving_run(q, args, dev, data, r, args.serve_curve_seconds)
         curve.append({k: rec[k] for k in ("offered_rate", "sustained", "windows", "p50_us", "p99_us", "p999_us",
-                                          "mismatch_vs_batch")})
+                                          "submit_delay_p99_us", "library_p99_us", "mismatch_vs_batch")})
     main["latency_vs_load"] = curve
     return main
 
