@@ -149,3 +149,28 @@ def test_window_graph_validates_on_the_host(L):
     h = C.c_void_p()
     assert L.qec_graph_create_window(None, 0, 4, None, C.byref(h)) == q.QEC_EINVAL and not h.value
     assert L.qec_graph_create_window(C.c_void_p(16), 0, 4, None, None) == q.QEC_EINVAL
+
+
+def test_tuning_knobs_validate_keep_and_restore(L):
+    """qec_set_tuning / qec_get_tuning on the host: a positive value sets a
+    knob, zero keeps it, a negative value restores its default; team sizes
+    other than 1, 4 and 16 and out-of-range values are refused without
+    changing anything."""
+    default = q.get_tuning()
+    try:
+        q.set_tuning(warps_per_block=2, team_warps=4, kcap=700, team_split_events=48)
+        t = q.get_tuning()
+        assert (t["warps_per_block"], t["team_warps"], t["kcap"], t["team_split_events"]) == (2, 4, 700, 48)
+        q.set_tuning(band_factor=2)   # zero keeps the others
+        t2 = q.get_tuning()
+        assert t2["band_factor"] == 2 and t2["team_warps"] == 4 and t2["kcap"] == 700
+        for bad in (dict(team_warps=8), dict(team_warps=2), dict(warps_per_block=33), dict(blocks_per_sm=65),
+                    dict(band_factor=65), dict(kcap=(1 << 18) + 1)):
+            with pytest.raises(RuntimeError):
+                q.set_tuning(**bad)
+            assert q.get_tuning() == t2, bad
+        q.set_tuning(warps_per_block=-1, team_warps=-1, kcap=-1, team_split_events=-1, band_factor=-1)
+        assert q.get_tuning() == default
+    finally:
+        q.set_tuning(warps_per_block=-1, blocks_per_sm=-1, band_factor=-1, kcap=-1, max_events=-1, team_warps=-1,
+                     team_min_detectors=-1, team_split_events=-1)
