@@ -302,7 +302,7 @@ int qec_decode_plain(const qec_graph *g, const uint32_t *syndromes, int64_t num_
  * binding; all have safe defaults).  In qec_set_tuning a positive value sets
  * a knob, zero keeps its current value and a negative value restores the
  * default (warps_per_block 4, blocks_per_sm 0 = as many as fit, band_factor 1,
- * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, or to 64 .. 2048 for graphs
+ * kcap 0 = num_detectors / 16 clamped to 64 .. 1024, or to 64 .. 4096 for graphs
  * of at least 32,768 detectors, max_events 4e6,
  * team_warps 0 = automatic, team_min_detectors 2048, team_split_events 1:
  * every shot of a block goes to the whole block; on a GB300 the autotuner's

@@ -314,13 +314,15 @@ void ws_free(Workspace &w) {
 constexpr int kTeamMidDetectors = 32768;
 
 // Default detection events per main-pass slab: num_detectors / 16, clamped to
-// 64 .. 1024, or to 64 .. 2048 for graphs of at least kTeamMidDetectors
-// detectors (a d = 51 window at p = 0.003 holds ~1,200 events; past kcap a
-// shot goes to the overflow pass, which has one team per SM).
-int kcap_for(int nmax, const qec_tuning &t) {
+// 64 .. 1024, or to 64 .. 4096 when block-wide teams decode a graph of at least
+// kTeamMidDetectors detectors (those launches hold one slab per resident block
+// only; a d = 51 window holds ~1,200 events at p = 0.003 and ~1,900 at
+// p = 0.005; past kcap a shot goes to the overflow pass, which has one team
+// per SM).
+int kcap_for(int nmax, const qec_tuning &t, bool blocks) {
     if (t.kcap > 0) return std::min(t.kcap, std::max(1, nmax));
     int k = nmax / 16;
-    k = std::max(64, std::min(nmax >= kTeamMidDetectors ? 2048 : 1024, k));
+    k = std::max(64, std::min(blocks && nmax >= kTeamMidDetectors ? 4096 : 1024, k));
     return std::min(k, std::max(nmax, 1));
 }
 
@@ -777,16 +779,6 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
     }
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int sms = sm_count(dev);
-    const int kcap = kcap_for(nmax, tune);
-    SlabCaps caps = qec::caps_for_kcap(kcap);
-    // overflow slabs: four times the events (a default capacity above 1,024
-    // keeps the overflow slabs at 4,096 events, as with a 1,024 main pass)
-    const int kcap2 = (tune.kcap > 0 || kcap <= 1024) ? std::min(nmax, 4 * kcap) : std::min(nmax, 4096);
-    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, kcap2), 3);
-    int wmax_words = 0;
-    for (int i = 0; i < num_graphs; i++) wmax_words = std::max(wmax_words, graphs[i]->words);
-    caps.wcap = std::max(caps.wcap, wmax_words);
-    caps2.wcap = std::max(caps2.wcap, wmax_words);
     const int wpb = std::max(1, std::min(tune.warps_per_block, qec::max_block_threads() / 32));
     int bps = tune.blocks_per_sm;
     if (bps <= 0) bps = qec::occupancy_blocks(32 * wpb);
@@ -810,13 +802,26 @@ static int decode_common(const qec_graph *const *graphs, int32_t num_graphs, con
         }
     }
     if (window && team == qec::TEAM_MID) team = 1;
+    const int kcap = kcap_for(nmax, tune, team > 1 && !plain);
+    SlabCaps caps = qec::caps_for_kcap(kcap);
+    // overflow slabs: four times the events (a default capacity above 1,024
+    // keeps the overflow slabs at 4,096 events, as with a 1,024 main pass)
+    const int kcap2 = (tune.kcap > 0 || kcap <= 1024) ? std::min(nmax, 4 * kcap) : std::min(nmax, 4096);
+    SlabCaps caps2 = qec::caps_for_kcap(std::max(kcap, kcap2), 3);
+    int wmax_words = 0;
+    for (int i = 0; i < num_graphs; i++) wmax_words = std::max(wmax_words, graphs[i]->words);
+    caps.wcap = std::max(caps.wcap, wmax_words);
+    caps2.wcap = std::max(caps2.wcap, wmax_words);
     // slabs: one per warp of the main pass (one warp per shot) or one per
     // resident block (one block per shot); the overflow pass has one per SM
     long long nwarps = plain ? 1 : (long long)sms * bps * wpb;
     long long nteams = nwarps;
     if (team > 1 && !plain) {
         nteams = std::min<long long>((long long)sms * qec::team_occupancy_blocks(team), std::max<long long>(num_shots, 1));
-        nwarps = std::max(nwarps, nteams);
+        // slabs for every resident one-warp team (so that a one-warp call
+        // after this one reuses them), except for the largest graphs, whose
+        // slabs are big: there only the blocks launched get one
+        nwarps = nmax >= kTeamMidDetectors ? nteams : std::max(nwarps, nteams);
     }
     long long nwarps2 = plain ? 1 : (long long)sms;
     if (plain) caps = caps2;
